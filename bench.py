@@ -1,0 +1,317 @@
+"""Benchmark: HVPs/s (loss + gradient + HVP per call) of the brickwall workload
+n = 20, L = 16 (K = 152 gates), N_s = 64 Haar product states, complex64 window
+passes with FP64 accumulation, on synthetic seeded inputs.
+
+One step = one full evaluation (every window pass plus the FP64 post-
+processing) of the whole workload. `value` is measured with the inputs
+resident in HBM (stream-ordered device-pointer call replaying the captured
+CUDA graph, CUDA events on the library's stream); `e2e` times the host-memory
+C ABI call (G, V uploaded and every result downloaded each step).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU, and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=20, n_layers=16, n_samples=64, seed=0)
+METRIC = "HVPs/sec (loss+grad+HVP) at n=20,L=16,N_s=64; fraction of roofline"
+FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(w, steps=1, warmup=0, max_seconds=150.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    as many of the N_s samples as the host has cores, one thread each. Cost is
+    exactly linear in N_s (samples are independent), so HVPs/s = (sample /
+    N_s) / seconds."""
+    from oracle import oracle
+
+    cores = os.cpu_count() or 1
+    m = max(1, min(w.n_samples, cores))
+    sub = w.psi1q[:m]
+    phi = oracle.reference_states(w.n, w.n_layers, w.Uref, sub)
+    stride = max(1, int(round(w.K ** 0.5)))
+    times = []
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        oracle.evaluate(w.n, w.n_layers, w.G, w.V, sub, phi, threads=m, ckpt_stride=stride)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+        if sum(times) > max_seconds:
+            break
+    sec = statistics.median(times)
+    return dict(value=(m / w.n_samples) / sec, unit="HVPs/s", cores=m, kind="oracle",
+                sample=f"{m} of {w.n_samples} samples (n={w.n}, L={w.n_layers}), {m} threads, "
+                       f"checkpoint stride {stride}; {sec:.2f} s per sample batch, scaled by {m}/{w.n_samples}",
+                seconds_per_step=sec, steps=len(times))
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return 0
+    from paper_2604_20384_gb300.inputs import make_workload
+
+    w = make_workload(**WORKLOAD)
+    # Each step is one oracle run over a bounded sample (one sample per core);
+    # warm-up is capped at one step and the timed steps at what fits ~150 s.
+    cb = cpu_baseline(w, steps=args.steps, warmup=min(args.warmup, 1), max_seconds=150.0)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "HVPs/s", "n_gpus": world,
+            "steps": cb["steps"], "warmup": min(args.warmup, 1),
+            "ms_per_step": 1000.0 * cb["seconds_per_step"] * w.n_samples / cb["cores"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152)", "n": 20, "L": 16, "N_s": 64},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": "HVPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the unfused FP64 comparison sweep")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2604_20384_gb300 import native
+    from paper_2604_20384_gb300.inputs import make_workload
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = make_workload(**WORKLOAD)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
+                         stream=stream.cuda_stream)
+    K = w.K
+    G_dev = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
+    V_dev = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
+    loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad_dev = torch.zeros(32 * K, dtype=torch.float64, device=dev)
+    hvp_dev = torch.zeros(32 * K, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize(dev)
+
+    def step():
+        ctx.hvp_dev(G_dev.data_ptr(), V_dev.data_ptr(), loss_dev.data_ptr(), grad_dev.data_ptr(),
+                    hvp_dev.data_ptr())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    info = ctx.plan_info()
+
+    # ---------------------------------------------------------- timed region
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # ------------------------------------------------ end to end (host API)
+    Gh = w.G.view(np.float64).reshape(-1).copy()
+    Vh = w.V.view(np.float64).reshape(-1).copy()
+    for _ in range(2):
+        ctx.hvp(Gh, Vh)
+    e2e_steps = max(3, min(args.steps, 20))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.hvp(Gh, Vh)
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    res_doubles = 2 + 4 * w.n_samples + 4 * 32 * K
+    e2e = {"value": world * 1000.0 / e2e_ms, "unit": "HVPs/s", "h2d_bytes_per_step": 2 * 32 * K * 8,
+           "d2h_bytes_per_step": res_doubles * 8 + 4, "ms_per_step": e2e_ms}
+
+    # ------------------------------------------- per-launch roofline (events)
+    prof = ctx.profile(G_dev.data_ptr(), V_dev.data_ptr())
+    kinds = prof["kind"]
+    by_kind = {}
+    for k in sorted(set(kinds.tolist())):
+        sel = kinds == k
+        by_kind[native.KINDS[k]] = dict(launches=int(sel.sum()), ms=float(prof["ms"][sel].sum()),
+                                        flops=float(prof["flops"][sel].sum()),
+                                        bytes=float(prof["bytes"][sel].sum()))
+    total_ms = float(prof["ms"].sum())
+    # Dominant kernel: the window-pass kernel (forward, turnaround and backward
+    # passes are one kernel); its arithmetic is FP32 SIMT, so the roofline is
+    # the FP32 lane rate at the maximum SM clock.
+    pass_kinds = [k for k in by_kind if k.startswith("pass_")]
+    p_ms = sum(by_kind[k]["ms"] for k in pass_kinds)
+    p_fl = sum(by_kind[k]["flops"] for k in pass_kinds)
+    p_by = sum(by_kind[k]["bytes"] for k in pass_kinds)
+    p_n = sum(by_kind[k]["launches"] for k in pass_kinds)
+    peaks, src = _peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s
+    achieved = p_fl / (p_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "tiled_pass_kernel<true,256> (all window passes)",
+                "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
+                "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
+                "hbm": {"achieved_gbs": p_by / (p_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
+                        "frac": (p_by / (p_ms / 1e3) / 1e9) / peaks.get("hbm_gbs", 6800.0),
+                        "peak_source": src}}
+
+    line = {"metric": METRIC, "value": value, "unit": "HVPs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic (seeded Haar brickwall, Haar product states)",
+            "config": {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152), complex64 window passes, "
+                                   "FP64 accumulation", "n": 20, "L": 16, "N_s": 64, "K": K,
+                       "window": info["window"], "passes": info["passes"],
+                       "checkpoint_stride": info["checkpoint_stride"], "tiles_per_cta": info["tiles_per_cta"],
+                       "l2": "inputs larger than L2 (512 MiB per state set, 129 MB L2)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": info["launches_per_hvp"] * args.steps,
+            "clocks": clocks, "per_kind": by_kind}
+
+    # ------------------------------------------ unfused FP64 sweep, same GPU
+    if not args.no_fp64 and rank == 0:
+        ctx.close()
+        with native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c128", device=local,
+                            stream=stream.cuda_stream) as c2:
+            c2.hvp_dev(G_dev.data_ptr(), V_dev.data_ptr(), None, None, None)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                c2.hvp_dev(G_dev.data_ptr(), V_dev.data_ptr(), None, None, None)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            f_ms = e0.elapsed_time(e1) / 2
+        line["fp64_unfused"] = {"value": 1000.0 / f_ms, "unit": "HVPs/s", "ms_per_step": f_ms,
+                                "speedup_of_value": value / world / (1000.0 / f_ms)}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w).items() if k not in ("seconds_per_step", "steps")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * hvp.h - C ABI of the GB300 (sm_103a) library for the sampled
+ * Hilbert-Schmidt loss of a brickwall circuit, its complex gradient and its
+ * Hessian-vector product by recursive tangent-state propagation
+ * (arXiv 2604.20384).
+ *
+ * Problem (Sec. 3.1, Eq. HST; Sec. 4.1, Eq. costHS; Alg. 2 "Require" line):
+ * given a brickwall of K two-qubit gates G = (G^[1], ..., G^[K]) on n qubits,
+ * N_s product input states psi_s and reference states phi_s = U_ref psi_s,
+ *     C(G) = 1 - (1/N_s) sum_s |phi_s^dagger G_K ... G_1 psi_s|^2 .
+ * The library returns C, the complex gradient grad C (Eq. grad-real:
+ * dC/dRe + i dC/dIm per matrix entry) and the HVP H C[V] = D(grad C)[V]
+ * along a direction V (Eq. FoR), optionally projected to the tangent space
+ * of U(4)^K (App. F, Eq. projec).
+ *
+ * Conventions for every array (the paper is silent on them):
+ *   - complex numbers are interleaved (re, im) doubles;
+ *   - qubit 0 is the most significant bit of an amplitude index;
+ *   - layer l (1-based) has offset (l-1) mod 2 and gates on qubits (i, i+1),
+ *     i = offset, offset+2, ..., i+1 <= n-1; gates are numbered layer-major,
+ *     then by i; K = hvp_num_gates(n, n_layers);
+ *   - a gate is a 4x4 row-major matrix indexed by 2 b_i + b_{i+1};
+ *     G, V, grad and hvp arrays hold K*16 complex numbers = K*32 doubles;
+ *   - psi_1q holds N_s*n single-qubit states (2 complex each) = N_s*n*4
+ *     doubles, psi_s = psi_{s,0} (x) ... (x) psi_{s,n-1};
+ *   - a state vector holds 2^n complex numbers.
+ *
+ * Ownership: the caller owns every array it passes. The library copies
+ * inputs and never keeps a caller pointer after a call returns. A context
+ * owns all device memory it allocates; hvp_free releases it.
+ *
+ * Errors: every int-returning call returns HVP_OK (0) or a negative code;
+ * hvp_last_error gives a message. Calls on one context must not overlap;
+ * distinct contexts are independent.
+ *
+ * Gates are not required to be unitary (finite differences evaluate G + hV);
+ * they must be invertible, because the backward sweep recomputes earlier
+ * forward states with G^-1 inside each window pass. The Riemannian outputs
+ * assume unitary gates.
+ */
+#ifndef HVP_H
+#define HVP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HVP_OK 0
+#define HVP_EINVAL (-1)      /* bad shape, flag, size or NULL pointer          */
+#define HVP_ENOMEM (-2)      /* device or host allocation failed               */
+#define HVP_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed    */
+#define HVP_ETIMEOUT (-4)    /* a bounded device-side wait expired             */
+#define HVP_ENONFINITE (-5)  /* NaN/Inf in the inputs or a singular gate       */
+
+/* precision */
+#define HVP_C64 0   /* complex64 state sweeps, FP64 per-gate accumulation   */
+#define HVP_C128 1  /* complex128 sweeps and FP64 accumulation             */
+
+/* flags */
+#define HVP_RIEMANNIAN 1  /* grad/hvp outputs are the Riemannian forms (App. F) */
+#define HVP_PHI_GIVEN 2   /* ref_data holds phi_s (N_s x 2^n) instead of U_ref */
+#define HVP_UNFUSED 4     /* one kernel launch per gate (the plain schedule)    */
+#define HVP_NO_GRAPH 8    /* launch kernels directly instead of a CUDA graph   */
+
+typedef struct hvp_ctx hvp_ctx;
+
+typedef struct {
+    int n;                 /* qubits, 2..30                                    */
+    int n_layers;          /* brickwall layers L >= 1                          */
+    int n_samples;         /* N_s >= 1                                         */
+    int precision;         /* HVP_C64 or HVP_C128                              */
+    int flags;             /* HVP_* flags, or-ed                               */
+    int checkpoint_stride; /* forward checkpoints every this many window
+                              passes, the others recomputed; 0 = automatic     */
+    int window;            /* local qubits per shared-memory tile; 0 = auto    */
+    int device;            /* CUDA device ordinal                              */
+    void *stream;          /* cudaStream_t for all work; NULL = own stream     */
+} hvp_config;
+
+/* Number of gates K of an open-boundary brickwall (Sec. 3.1); -1 if n < 2
+ * or n_layers < 1. No GPU needed. */
+int hvp_num_gates(int n, int n_layers);
+
+/* Creates a context: validates cfg, allocates device memory, uploads the
+ * input states and computes phi_s = U_ref psi_s once (Sec. 3.1, Eq.
+ * cost-summands: phi = U_ref psi) unless HVP_PHI_GIVEN.
+ *   psi_1q   : host, N_s*n*4 doubles (see conventions).
+ *   ref_data : host, U_ref gates (K*32 doubles), or with HVP_PHI_GIVEN the
+ *              reference states phi_s (N_s * 2^n * 2 doubles).
+ * On failure *out is NULL; the message is available from hvp_last_error(NULL)
+ * on the calling thread. */
+int hvp_init(hvp_ctx **out, const hvp_config *cfg, const double *psi_1q,
+             const double *ref_data);
+
+/* Loss and gradient (Alg. 1 without tangents, Alg. 2 first two steps).
+ *   G    : host, K*32 doubles.
+ *   loss : host, 1 double (may be NULL).
+ *   grad : host, K*32 doubles (may be NULL); Euclidean, or Riemannian with
+ *          HVP_RIEMANNIAN.
+ * Blocks until the results are on the host. */
+int hvp_loss_grad(hvp_ctx *ctx, const double *G, double *loss, double *grad);
+
+/* Loss, gradient and HVP along V in one forward/backward sweep pair
+ * (Alg. 1 and Alg. 2; Eq. dfis, dbis, overlap-hvp, hvp-costHS).
+ *   G, V : host, K*32 doubles each.
+ *   loss, grad, hvp : host outputs (each may be NULL); grad and hvp are
+ *          Euclidean, or Riemannian with HVP_RIEMANNIAN.
+ * Blocks until the results are on the host. */
+int hvp_hvp(hvp_ctx *ctx, const double *G, const double *V, double *loss,
+            double *grad, double *hvp);
+
+/* Stream-ordered variants on device memory (for framework integration):
+ * inputs and outputs are device pointers of the same sizes as above; V_dev
+ * may be NULL (loss and gradient only); any output may be NULL. Work is
+ * enqueued on the context's stream and the call returns without waiting. */
+int hvp_hvp_dev(hvp_ctx *ctx, const double *G_dev, const double *V_dev,
+                double *loss_dev, double *grad_dev, double *hvp_dev);
+
+/* Results of the last completed call, copied to host memory (synchronises
+ * the context's stream):
+ *   HVP_OUT_T, HVP_OUT_OMEGA : N_s complex (2*N_s doubles), the overlaps
+ *        T_s = phi_s^dagger G psi_s and Omega_s = D T_s[V] (Eq. Omega);
+ *   HVP_OUT_GRAD_E, HVP_OUT_HVP_E : Euclidean forms, K*32 doubles;
+ *   HVP_OUT_GRAD_R, HVP_OUT_HVP_R : Riemannian forms, K*32 doubles;
+ *   HVP_OUT_LOSS : 1 double;
+ *   HVP_OUT_ENV : per-sample environments dT_s/dG_k and D(dT_s/dG_k)[V],
+ *        N_s*K*32 complex (N_s*K*64 doubles; the 16 entries of E then the
+ *        16 of DE per gate). */
+#define HVP_OUT_T 1
+#define HVP_OUT_OMEGA 2
+#define HVP_OUT_GRAD_E 3
+#define HVP_OUT_HVP_E 4
+#define HVP_OUT_GRAD_R 5
+#define HVP_OUT_HVP_R 6
+#define HVP_OUT_LOSS 7
+#define HVP_OUT_ENV 8
+int hvp_get(hvp_ctx *ctx, int what, double *out);
+
+/* Description of the execution plan of a context (host memory):
+ *   info[0] = K, info[1] = number of window passes P, info[2] = window
+ *   (local qubits per tile), info[3] = checkpoint stride, info[4] = kernel
+ *   launches of the last hvp call, info[5] = device memory held by the
+ *   context in MiB, info[6] = tiles per CTA, info[7] = CTAs per sample. */
+int hvp_plan_info(const hvp_ctx *ctx, long long info[8]);
+
+/* Window-pass plan of a brickwall without a context or GPU (for tests and
+ * tools): fills pass_of_gate[K] with the pass index of each gate and returns
+ * the number of passes P, or a negative code. window = local qubits per tile
+ * (n <= window gives a single pass), low_bits = address bits every tile keeps
+ * contiguous. */
+int hvp_plan_brickwall(int n, int n_layers, int window, int low_bits, int *pass_of_gate);
+
+/* Runs one evaluation (V_dev NULL: loss and gradient only) launching its
+ * kernels one by one with a CUDA event after each launch on the context's
+ * stream, and reports per launch: ms[i] the event-to-event device time,
+ * kind[i] (HVP_K_* below), flops[i] the algorithmic floating-point
+ * operations of that launch (8 per complex multiply-add; per amplitude and
+ * gate 12 complex multiply-adds forward and 36 backward with tangents, 4 and
+ * 12 without) and bytes[i] its algorithmic HBM bytes (every state element the
+ * launch needs read once and every result written once). Arrays hold
+ * max_launches entries (host memory).
+ * Returns the number of launches (> max_launches: arrays truncated) or a
+ * negative code. Synchronises the stream. */
+#define HVP_K_PREP 0
+#define HVP_K_PASS_FWD 1
+#define HVP_K_PASS_TURN 2
+#define HVP_K_PASS_BWD 3
+#define HVP_K_GATE_INIT 4
+#define HVP_K_GATE_FWD 5
+#define HVP_K_GATE_PHI 6
+#define HVP_K_GATE_BWD 7
+#define HVP_K_POST 8
+int hvp_profile(hvp_ctx *ctx, const double *G_dev, const double *V_dev, int max_launches,
+                float *ms, int *kind, double *flops, double *bytes);
+
+/* Releases the context and all its device memory; NULL is ignored. */
+void hvp_free(hvp_ctx *ctx);
+
+/* Message of the last failed call on ctx, or with ctx == NULL the last
+ * failure of hvp_init on the calling thread. Never NULL. */
+const char *hvp_last_error(const hvp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HVP_H */

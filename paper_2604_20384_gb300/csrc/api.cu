@@ -1,0 +1,669 @@
+// C ABI of libhvp: contexts, device memory, the launch schedule of one
+// loss/gradient/HVP evaluation and its capture into CUDA graphs.
+//
+// Schedule of one evaluation on the window-pass path (P passes, Alg. 1):
+//   prep (G^-1, G^dag, V^dag in FP64, FP32 copies)
+//   forward passes 0 .. P-2, each storing its output states as a checkpoint
+//   turnaround pass P-1: forward through its gates, then backward through
+//       them with co-states (phi_s, 0)
+//   backward passes P-2 .. 0, each reloading the forward checkpoint at its end
+//   FP64 post-processing (reduction, T_s, Omega_s, loss, grad, HVP, App. F)
+// With a checkpoint stride c > 1 only every c-th boundary is kept and the
+// others are recomputed segment by segment before the backward passes need
+// them.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/hvp.h"
+#include "internal.h"
+
+using namespace hvp;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+std::string fmt(const char* f, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    return buf;
+}
+
+}  // namespace
+
+struct hvp_ctx {
+    hvp_config cfg{};
+    int K = 0;
+    bool dbl = false, unfused = false;
+    Plan plan;
+    int w = 0, threads = 256, tiles_per_cta = 1, cx_count = 1, stride = 1, P = 0, max_gates = 0;
+    int n_slots = 0, s0_last = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+    DevPass* d_pass = nullptr;
+    DevGate* d_gates = nullptr;
+    double2* d_G = nullptr;
+    double2* d_V = nullptr;
+    void* d_mats = nullptr;
+    void* d_psi1q = nullptr;
+    void* d_phi = nullptr;
+    std::vector<void*> ckpt;   // boundary j -> stored buffer or nullptr
+    std::vector<void*> slots;  // recomputed boundaries of one segment
+    void* d_scratch = nullptr; // non-stored boundaries of the first forward sweep
+    void* d_co = nullptr;      // co-states (a, b)
+    void* d_x = nullptr;       // unfused forward states
+    double* d_partial = nullptr;
+    double* d_env = nullptr;
+    double* d_res = nullptr;
+    int* d_status = nullptr;
+    double* h_in = nullptr;
+    double* h_res = nullptr;
+    int* h_status = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    size_t bytes = 0;
+    size_t res_len = 0;
+    int launches_per_call[2] = {0, 0};
+    std::string err;
+    // per-launch profiling (hvp_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    std::vector<double> prof_flops, prof_bytes;
+
+    size_t off_T() const { return 2; }
+    size_t off_Om() const { return 2 + 2 * (size_t)cfg.n_samples; }
+    size_t off_ge() const { return 2 + 4 * (size_t)cfg.n_samples; }
+    size_t off_he() const { return off_ge() + 32 * (size_t)K; }
+    size_t off_gr() const { return off_he() + 32 * (size_t)K; }
+    size_t off_hr() const { return off_gr() + 32 * (size_t)K; }
+};
+
+namespace {
+
+int fail(hvp_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                           \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HVP_ENOMEM : HVP_ECUDA,               \
+                        fmt("%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__));   \
+    } while (0)
+
+// Records an event after a launch when profiling.
+int prof_mark(hvp_ctx* c, int kind, double flops, double bytes) {
+    if (!c->prof) return HVP_OK;
+    cudaEvent_t e;
+    CUDA_TRY(c, cudaEventCreate(&e));
+    c->prof_ev.push_back(e);
+    CUDA_TRY(c, cudaEventRecord(e, c->stream));
+    c->prof_kind.push_back(kind);
+    c->prof_flops.push_back(flops);
+    c->prof_bytes.push_back(bytes);
+    return HVP_OK;
+}
+
+int dalloc(hvp_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return HVP_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, HVP_ENOMEM, fmt("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e)));
+    }
+    c->allocs.push_back(*p);
+    c->bytes += bytes;
+    return HVP_OK;
+}
+
+bool all_finite(const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+size_t state_elt(const hvp_ctx* c) { return c->dbl ? 32 : 16; }   // (psi, dpsi) per amplitude
+
+// ------------------------------------------------------------ tiled schedule
+
+const void* boundary_in(hvp_ctx* c, int j) {   // forward states after pass j-1
+    if (j == 0) return nullptr;                // generated in-kernel
+    if (c->ckpt[j]) return c->ckpt[j];
+    if (j > c->s0_last) return c->slots[j - c->s0_last - 1];
+    return c->d_scratch;
+}
+
+int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool tan, int ld_out, int st_out,
+               const void* mats, const void* phi) {
+    TiledArgs a{};
+    a.pass = c->d_pass + p;
+    a.gates = c->d_gates;
+    a.mats = reinterpret_cast<const Mats32*>(mats);
+    a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
+    a.xin = xin;
+    a.xout = xout;
+    a.phi = reinterpret_cast<const float2*>(phi);
+    a.cin = c->d_co;
+    a.cout = c->d_co;
+    a.partial = c->d_partial;
+    a.n = c->cfg.n;
+    a.n_samples = c->cfg.n_samples;
+    a.mode = mode;
+    a.tiles_per_cta = c->tiles_per_cta;
+    a.cx_count = c->cx_count;
+    a.ld_out_tab = ld_out;
+    a.st_out_tab = st_out;
+    const int ng = (int)c->plan.passes[p].gates.size();
+    CUDA_TRY(c, launch_tiled(a, tan, c->w, c->threads, std::max(ng, 1), c->stream));
+    if (c->prof) {
+        // Algorithmic work: 12 (36) complex MACs per amplitude per gate forward
+        // (backward) with tangents, 4 (12) without; 8 flops per complex MAC.
+        const double amps = (double)((size_t)1 << c->cfg.n) * c->cfg.n_samples;
+        const double elt = tan ? 16.0 : 8.0;
+        double fl = 0, by = 0;
+        if (mode & M_FWD) fl += amps * ng * (tan ? 96.0 : 32.0);
+        if (mode & M_BWD) fl += amps * ng * (tan ? 288.0 : 96.0);
+        if (!(mode & M_GEN)) by += amps * elt;
+        if (mode & M_STORE_F) by += amps * elt;
+        if (mode & M_BWD) by += amps * ((mode & M_LOAD_PHI) ? 8.0 : elt);
+        if (mode & M_STORE_B) by += amps * elt;
+        const int kind = (mode & M_BWD) ? ((mode & M_FWD) ? HVP_K_PASS_TURN : HVP_K_PASS_BWD) : HVP_K_PASS_FWD;
+        return prof_mark(c, kind, fl, by);
+    }
+    return HVP_OK;
+}
+
+int enqueue_tiled(hvp_ctx* c, bool tan, int* launches) {
+    const int P = c->P, cs = c->stride;
+    int rc, L = 0;
+    // First forward sweep.
+    for (int p = 0; p + 1 < P; ++p) {
+        const int j = p + 1;
+        void* out = c->ckpt[j] ? c->ckpt[j] : (j > c->s0_last ? c->slots[j - c->s0_last - 1] : c->d_scratch);
+        const int mode = (p == 0 ? M_GEN : 0) | M_FWD | M_STORE_F;
+        if ((rc = tiled_pass(c, p, mode, boundary_in(c, p), out, tan, 0, 1, c->d_mats, c->d_phi))) return rc;
+        ++L;
+    }
+    // Backward, segment by segment from the end.
+    const int nseg = (P - 1) / cs + 1;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int s0 = sg * cs, s1 = std::min(s0 + cs, P);
+        if (s0 != c->s0_last) {   // recompute boundaries s0+1 .. s1-1 into the slots
+            for (int p = s0; p + 1 < s1; ++p) {
+                const void* in = p == s0 ? boundary_in(c, s0) : c->slots[p - s0 - 1];
+                const int mode = (p == 0 ? M_GEN : 0) | M_FWD | M_STORE_F;
+                if ((rc = tiled_pass(c, p, mode, in, c->slots[p - s0], tan, 0, 1, c->d_mats, c->d_phi))) return rc;
+                ++L;
+            }
+        }
+        for (int p = s1 - 1; p >= s0; --p) {
+            if (p == P - 1) {
+                const int mode = (P == 1 ? M_GEN : 0) | M_FWD | M_BWD | M_LOAD_PHI | (P > 1 ? M_STORE_B : 0);
+                const void* in = boundary_in(c, P - 1);
+                if ((rc = tiled_pass(c, p, mode, in, nullptr, tan, 0, 0, c->d_mats, c->d_phi))) return rc;
+            } else {
+                const void* in = (p + 1 == s1) ? c->ckpt[s1] : c->slots[p - s0];
+                const int mode = M_BWD | (p > 0 ? M_STORE_B : 0);
+                if ((rc = tiled_pass(c, p, mode, in, nullptr, tan, 1, 0, c->d_mats, c->d_phi))) return rc;
+            }
+            ++L;
+        }
+    }
+    *launches = L;
+    return HVP_OK;
+}
+
+int enqueue_unfused(hvp_ctx* c, bool tan, int* launches) {
+    const int n = c->cfg.n, ns = c->cfg.n_samples, K = c->K;
+    int L = 0;
+    const double amps = (double)((size_t)1 << n) * ns;
+    const double cb = c->dbl ? 16.0 : 8.0, elt = (tan ? 2.0 : 1.0) * cb;
+    int rc;
+    CUDA_TRY(c, unfused_init(c->dbl, c->d_psi1q, c->d_x, n, ns, tan, c->stream));
+    if ((rc = prof_mark(c, HVP_K_GATE_INIT, 0.0, amps * elt))) return rc;
+    ++L;
+    for (int k = 0; k < K; ++k) {
+        CUDA_TRY(c, unfused_fwd_gate(c->dbl, c->d_mats, k, c->plan.first_qubit[k], c->d_x, n, ns, tan, c->stream));
+        if ((rc = prof_mark(c, HVP_K_GATE_FWD, amps * (tan ? 96.0 : 32.0), 2 * amps * elt))) return rc;
+        ++L;
+    }
+    CUDA_TRY(c, unfused_load_phi(c->dbl, c->d_phi, c->d_co, n, ns, tan, c->stream));
+    if ((rc = prof_mark(c, HVP_K_GATE_PHI, 0.0, amps * (cb + elt)))) return rc;
+    ++L;
+    for (int k = K - 1; k >= 0; --k) {
+        CUDA_TRY(c, unfused_bwd_gate(c->dbl, c->d_mats, k, c->plan.first_qubit[k], c->d_x, c->d_co, c->d_partial, n,
+                                     ns, c->cx_count, tan, c->stream));
+        if ((rc = prof_mark(c, HVP_K_GATE_BWD, amps * (tan ? 288.0 : 96.0), 4 * amps * elt))) return rc;
+        ++L;
+    }
+    *launches = L;
+    return HVP_OK;
+}
+
+int enqueue_all(hvp_ctx* c, bool tan) {
+    int L = 0, rc;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, launch_prep(c->d_G, tan ? c->d_V : nullptr, c->d_mats, c->dbl, c->K, c->d_status, c->stream));
+    if ((rc = prof_mark(c, HVP_K_PREP, 0.0, 0.0))) return rc;
+    ++L;
+    int Ls = 0;
+    rc = c->unfused ? enqueue_unfused(c, tan, &Ls) : enqueue_tiled(c, tan, &Ls);
+    if (rc) return rc;
+    L += Ls;
+    PostArgs p{};
+    p.partial = c->d_partial;
+    p.env = c->d_env;
+    p.G = c->d_G;
+    p.V = c->d_V;
+    p.T = reinterpret_cast<double2*>(c->d_res + c->off_T());
+    p.Omega = reinterpret_cast<double2*>(c->d_res + c->off_Om());
+    p.loss = c->d_res;
+    p.grad_e = reinterpret_cast<double2*>(c->d_res + c->off_ge());
+    p.hvp_e = reinterpret_cast<double2*>(c->d_res + c->off_he());
+    p.grad_r = reinterpret_cast<double2*>(c->d_res + c->off_gr());
+    p.hvp_r = reinterpret_cast<double2*>(c->d_res + c->off_hr());
+    p.K = c->K;
+    p.n_samples = c->cfg.n_samples;
+    p.cx_count = c->cx_count;
+    p.tangent = tan ? 1 : 0;
+    CUDA_TRY(c, launch_post(p, c->stream));
+    if ((rc = prof_mark(c, HVP_K_POST, 0.0, 0.0))) return rc;
+    L += 4;
+    c->launches_per_call[tan ? 1 : 0] = L;
+    return HVP_OK;
+}
+
+// Runs one evaluation on the context's stream: replays the captured graph, or
+// launches directly when graphs are off or the stream is already capturing.
+int run(hvp_ctx* c, bool tan) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(c, cudaStreamIsCapturing(c->stream, &cap));
+    if ((c->cfg.flags & HVP_NO_GRAPH) || cap != cudaStreamCaptureStatusNone) return enqueue_all(c, tan);
+    cudaGraphExec_t& ge = c->gexec[tan ? 1 : 0];
+    if (!ge) {
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_all(c, tan);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(c, HVP_ECUDA, fmt("graph capture failed: %s", cudaGetErrorString(e)));
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ge = nullptr;
+            return fail(c, HVP_ECUDA, fmt("graph instantiation failed: %s", cudaGetErrorString(e)));
+        }
+    }
+    CUDA_TRY(c, cudaGraphLaunch(ge, c->stream));
+    return HVP_OK;
+}
+
+int compute_phi_from_uref(hvp_ctx* c, const double* uref) {
+    const int n = c->cfg.n, ns = c->cfg.n_samples;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, uref, 32 * sizeof(double) * c->K, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, launch_prep(c->d_G, nullptr, c->d_mats, c->dbl, c->K, c->d_status, c->stream));
+    if (c->unfused) {
+        CUDA_TRY(c, unfused_init(c->dbl, c->d_psi1q, c->d_phi, n, ns, false, c->stream));
+        for (int k = 0; k < c->K; ++k)
+            CUDA_TRY(c, unfused_fwd_gate(c->dbl, c->d_mats, k, c->plan.first_qubit[k], c->d_phi, n, ns, false,
+                                         c->stream));
+    } else {
+        // psi-only forward passes, in place on the phi buffer; the result ends in
+        // the layout of the last pass, which is where the turnaround pass reads it.
+        for (int p = 0; p < c->P; ++p) {
+            const int mode = (p == 0 ? M_GEN : 0) | M_FWD | M_STORE_F;
+            int rc = tiled_pass(c, p, mode, c->d_phi, c->d_phi, false, 0, 1, c->d_mats, nullptr);
+            if (rc) return rc;
+        }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (*c->h_status) return fail(c, HVP_ENONFINITE, "U_ref contains a non-finite or singular gate");
+    return HVP_OK;
+}
+
+// Tiles per CTA: about eight waves of CTAs over 152 SMs, every CTA on tiles of
+// one sample (its environment sums are per sample).
+int choose_tiling(hvp_ctx* c) {
+    const int ns = c->cfg.n_samples;
+    const long long tps = 1ll << (c->cfg.n - c->w);
+    long long cx = 1;
+    while (cx < tps && cx * ns < 8 * 152) cx *= 2;
+    c->cx_count = (int)cx;
+    c->tiles_per_cta = (int)(tps / cx);
+    return HVP_OK;
+}
+
+int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const double* ref) {
+    if (!cfg || !psi_1q || !ref) return fail(c, HVP_EINVAL, "hvp_init: NULL argument");
+    c->cfg = *cfg;
+    const int n = cfg->n, L = cfg->n_layers, ns = cfg->n_samples;
+    if (n < 2 || n > kMaxN) return fail(c, HVP_EINVAL, fmt("n = %d outside [2, %d]", n, kMaxN));
+    if (L < 1) return fail(c, HVP_EINVAL, "n_layers must be >= 1");
+    if (ns < 1) return fail(c, HVP_EINVAL, "n_samples must be >= 1");
+    if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
+    if (cfg->flags & ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH))
+        return fail(c, HVP_EINVAL, "unknown flag bits");
+    if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
+    if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))
+        return fail(c, HVP_EINVAL, "window must be 0 (auto) or in [6, 12]");
+    if (((size_t)1 << n) * (size_t)ns > ((size_t)1 << 34))
+        return fail(c, HVP_EINVAL, "2^n * n_samples above 2^34 amplitudes");
+    if (!all_finite(psi_1q, (size_t)ns * n * 4)) return fail(c, HVP_ENONFINITE, "psi_1q is not finite");
+    c->K = num_gates(n, L);
+    c->dbl = cfg->precision == HVP_C128;
+    c->unfused = c->dbl || (cfg->flags & HVP_UNFUSED);
+    const size_t dim = (size_t)1 << n;
+    if (cfg->flags & HVP_PHI_GIVEN) {
+        if (!all_finite(ref, dim * ns * 2)) return fail(c, HVP_ENONFINITE, "phi is not finite");
+    } else if (!all_finite(ref, 32 * (size_t)c->K)) {
+        return fail(c, HVP_ENONFINITE, "U_ref is not finite");
+    }
+
+    CUDA_TRY(c, cudaSetDevice(cfg->device));
+    if (cfg->stream) {
+        c->stream = (cudaStream_t)cfg->stream;
+    } else {
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+
+    // Plan.
+    int rc;
+    if (c->unfused) {
+        brickwall_layout(n, L, c->plan.first_qubit);
+        c->plan.n = n; c->plan.L = L; c->plan.K = c->K;
+        c->cx_count = unfused_cx_count(n, ns);
+        c->P = 0;
+    } else {
+        CUDA_TRY(c, tiled_set_smem_limits());
+        c->w = std::min(n, cfg->window ? cfg->window : 12);
+        if ((rc = make_plan(n, L, c->w, std::min(kLowBits, c->w - 1), c->plan))) return fail(c, rc, "planning failed");
+        c->P = (int)c->plan.passes.size();
+        for (auto& pp : c->plan.passes) c->max_gates = std::max(c->max_gates, (int)pp.gates.size());
+        choose_tiling(c);
+    }
+
+    // Device memory.
+    const size_t ctype = c->dbl ? 16 : 8;
+    if ((rc = dalloc(c, (void**)&c->d_G, 16 * 16 * (size_t)c->K))) return rc;
+    if ((rc = dalloc(c, (void**)&c->d_V, 16 * 16 * (size_t)c->K))) return rc;
+    if ((rc = dalloc(c, &c->d_mats, (c->dbl ? sizeof(Mats64) : sizeof(Mats32)) * (size_t)c->K))) return rc;
+    if ((rc = dalloc(c, &c->d_psi1q, ctype * 2 * (size_t)n * ns))) return rc;
+    if ((rc = dalloc(c, &c->d_phi, ctype * dim * ns))) return rc;
+    if ((rc = dalloc(c, &c->d_co, state_elt(c) * dim * ns))) return rc;
+    if ((rc = dalloc(c, (void**)&c->d_partial, 64 * sizeof(double) * (size_t)c->K * ns * c->cx_count))) return rc;
+    if ((rc = dalloc(c, (void**)&c->d_env, 64 * sizeof(double) * (size_t)c->K * ns))) return rc;
+    c->res_len = c->off_hr() + 32 * (size_t)c->K;
+    if ((rc = dalloc(c, (void**)&c->d_res, sizeof(double) * c->res_len))) return rc;
+    if ((rc = dalloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
+    CUDA_TRY(c, cudaMemset(c->d_V, 0, 16 * 16 * (size_t)c->K));
+    CUDA_TRY(c, cudaMemset(c->d_res, 0, sizeof(double) * c->res_len));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_in, sizeof(double) * 64 * (size_t)c->K));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_res, sizeof(double) * c->res_len));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_status, sizeof(int)));
+
+    if (c->unfused) {
+        if ((rc = dalloc(c, &c->d_x, state_elt(c) * dim * ns))) return rc;
+    } else {
+        std::vector<DevPass> dp;
+        std::vector<DevGate> dg;
+        build_dev_passes(c->plan, dp, dg);
+        if ((rc = dalloc(c, (void**)&c->d_pass, sizeof(DevPass) * dp.size()))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_gates, sizeof(DevGate) * std::max<size_t>(dg.size(), 1)))) return rc;
+        CUDA_TRY(c, cudaMemcpy(c->d_pass, dp.data(), sizeof(DevPass) * dp.size(), cudaMemcpyHostToDevice));
+        if (!dg.empty())
+            CUDA_TRY(c, cudaMemcpy(c->d_gates, dg.data(), sizeof(DevGate) * dg.size(), cudaMemcpyHostToDevice));
+        // Checkpoint stride: every boundary if memory allows, else the smallest
+        // stride that fits in 85% of the free device memory.
+        const int P = c->P;
+        const size_t sbytes = state_elt(c) * dim * ns;
+        size_t free_b = 0, total_b = 0;
+        CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
+        int cs = cfg->checkpoint_stride;
+        auto need = [&](int s) {
+            const int stored = (P - 1) / s;
+            const int s0_last = ((P - 1) / s) * s;
+            const int slots = std::max(s - 1, P - 1 - s0_last);
+            const bool scratch = s > 1 && s0_last > 1;
+            return sbytes * (size_t)(stored + slots + (scratch ? 1 : 0));
+        };
+        if (cs == 0) {
+            cs = 1;
+            while (cs < std::max(P, 1) && need(cs) > (size_t)(0.85 * (double)free_b)) ++cs;
+        }
+        cs = std::max(1, std::min(cs, std::max(P, 1)));
+        c->stride = cs;
+        c->s0_last = ((P - 1) / cs) * cs;
+        c->ckpt.assign(P + 1, nullptr);
+        for (int j = 1; j <= P - 1; ++j)
+            if (j % cs == 0)
+                if ((rc = dalloc(c, &c->ckpt[j], sbytes))) return rc;
+        c->n_slots = std::max(cs - 1, P - 1 - c->s0_last);
+        c->slots.assign(c->n_slots, nullptr);
+        for (int i = 0; i < c->n_slots; ++i)
+            if ((rc = dalloc(c, &c->slots[i], sbytes))) return rc;
+        if (cs > 1 && c->s0_last > 1)
+            if ((rc = dalloc(c, &c->d_scratch, sbytes))) return rc;
+    }
+
+    // Input states.
+    double* tmp = nullptr;
+    const size_t tmp_bytes = sizeof(double) * std::max((size_t)ns * n * 4, (cfg->flags & HVP_PHI_GIVEN) ? dim * ns * 2 : 0);
+    if (cudaMalloc((void**)&tmp, tmp_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, HVP_ENOMEM, "temporary input buffer");
+    }
+    struct TmpFree { double* p; ~TmpFree() { cudaFree(p); } } tmp_guard{tmp};
+    CUDA_TRY(c, cudaMemcpy(tmp, psi_1q, sizeof(double) * ns * n * 4, cudaMemcpyHostToDevice));
+    if (c->dbl) CUDA_TRY(c, cudaMemcpy(c->d_psi1q, tmp, sizeof(double) * ns * n * 4, cudaMemcpyDeviceToDevice));
+    else CUDA_TRY(c, launch_psi1q_convert(tmp, (float2*)c->d_psi1q, (size_t)ns * n * 2, c->stream));
+    if (cfg->flags & HVP_PHI_GIVEN) {
+        std::vector<int> pos(n);
+        if (c->unfused) {
+            for (int q = 0; q < n; ++q) pos[q] = n - 1 - q;
+        } else {
+            pos = c->plan.passes[c->P - 1].pos_in;
+        }
+        int* dpos = nullptr;
+        if ((rc = dalloc(c, (void**)&dpos, sizeof(int) * n))) return rc;
+        CUDA_TRY(c, cudaMemcpyAsync(tmp, ref, sizeof(double) * dim * ns * 2, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(dpos, pos.data(), sizeof(int) * n, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, launch_phi_permute((const double2*)tmp, c->d_phi, c->dbl, n, ns, dpos, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    } else {
+        if ((rc = compute_phi_from_uref(c, ref))) return rc;
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaGetLastError());
+    return HVP_OK;
+}
+
+int call_impl(hvp_ctx* c, const double* G, const double* V, double* loss, double* grad, double* hvp_out) {
+    if (!c) return HVP_EINVAL;
+    if (!G) return fail(c, HVP_EINVAL, "G is NULL");
+    const size_t n32 = 32 * (size_t)c->K;
+    const bool tan = V != nullptr;
+    if (!all_finite(G, n32) || (tan && !all_finite(V, n32))) return fail(c, HVP_ENONFINITE, "G or V is not finite");
+    std::memcpy(c->h_in, G, sizeof(double) * n32);
+    if (tan) std::memcpy(c->h_in + n32, V, sizeof(double) * n32);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, c->h_in, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
+    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->d_V, c->h_in + n32, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
+    int rc = run(c, tan);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_res, c->d_res, sizeof(double) * c->res_len, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (*c->h_status) return fail(c, HVP_ENONFINITE, "a gate is singular or not finite");
+    const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
+    const double* g = c->h_res + (riem ? c->off_gr() : c->off_ge());
+    const double* h = c->h_res + (riem ? c->off_hr() : c->off_he());
+    if (!all_finite(c->h_res, c->off_ge() + n32) || !all_finite(g, n32) || (tan && !all_finite(h, n32)))
+        return fail(c, HVP_ENONFINITE, "non-finite result");
+    if (loss) *loss = c->h_res[0];
+    if (grad) std::memcpy(grad, g, sizeof(double) * n32);
+    if (hvp_out && tan) std::memcpy(hvp_out, h, sizeof(double) * n32);
+    return HVP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hvp_init(hvp_ctx** out, const hvp_config* cfg, const double* psi_1q, const double* ref_data) {
+    if (!out) return fail(nullptr, HVP_EINVAL, "hvp_init: out is NULL");
+    *out = nullptr;
+    hvp_ctx* c = new (std::nothrow) hvp_ctx();
+    if (!c) return fail(nullptr, HVP_ENOMEM, "out of host memory");
+    int rc = init_impl(c, cfg, psi_1q, ref_data);
+    if (rc) {
+        g_init_error = c->err;
+        hvp_free(c);
+        return rc;
+    }
+    *out = c;
+    return HVP_OK;
+}
+
+int hvp_loss_grad(hvp_ctx* ctx, const double* G, double* loss, double* grad) {
+    return call_impl(ctx, G, nullptr, loss, grad, nullptr);
+}
+
+int hvp_hvp(hvp_ctx* ctx, const double* G, const double* V, double* loss, double* grad, double* hvp) {
+    if (ctx && !V) return fail(ctx, HVP_EINVAL, "V is NULL");
+    return call_impl(ctx, G, V, loss, grad, hvp);
+}
+
+int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* loss_dev, double* grad_dev,
+                double* hvp_dev) {
+    if (!c) return HVP_EINVAL;
+    if (!G_dev) return fail(c, HVP_EINVAL, "G_dev is NULL");
+    const size_t n32 = 32 * (size_t)c->K;
+    const bool tan = V_dev != nullptr;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->d_V, V_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    int rc = run(c, tan);
+    if (rc) return rc;
+    const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
+    if (loss_dev) CUDA_TRY(c, cudaMemcpyAsync(loss_dev, c->d_res, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (grad_dev)
+        CUDA_TRY(c, cudaMemcpyAsync(grad_dev, c->d_res + (riem ? c->off_gr() : c->off_ge()), sizeof(double) * n32,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    if (hvp_dev && tan)
+        CUDA_TRY(c, cudaMemcpyAsync(hvp_dev, c->d_res + (riem ? c->off_hr() : c->off_he()), sizeof(double) * n32,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    return HVP_OK;
+}
+
+int hvp_profile(hvp_ctx* c, const double* G_dev, const double* V_dev, int max_launches, float* ms, int* kind,
+                double* flops, double* bytes) {
+    if (!c || !G_dev || max_launches < 0) return HVP_EINVAL;
+    const size_t n32 = 32 * (size_t)c->K;
+    const bool tan = V_dev != nullptr;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->d_V, V_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    cudaEvent_t start;
+    CUDA_TRY(c, cudaEventCreate(&start));
+    CUDA_TRY(c, cudaEventRecord(start, c->stream));
+    c->prof = true;
+    int rc = enqueue_all(c, tan);
+    c->prof = false;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    int count = (int)c->prof_ev.size();
+    if (!rc && e == cudaSuccess) {
+        cudaEvent_t prev = start;
+        for (int i = 0; i < count; ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, prev, c->prof_ev[i]);
+            prev = c->prof_ev[i];
+            if (i < max_launches) {
+                if (ms) ms[i] = t;
+                if (kind) kind[i] = c->prof_kind[i];
+                if (flops) flops[i] = c->prof_flops[i];
+                if (bytes) bytes[i] = c->prof_bytes[i];
+            }
+        }
+    }
+    cudaEventDestroy(start);
+    for (auto ev : c->prof_ev) cudaEventDestroy(ev);
+    c->prof_ev.clear();
+    c->prof_kind.clear();
+    c->prof_flops.clear();
+    c->prof_bytes.clear();
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(c, HVP_ECUDA, fmt("profiling run failed: %s", cudaGetErrorString(e)));
+    return count;
+}
+
+int hvp_get(hvp_ctx* c, int what, double* out) {
+    if (!c || !out) return HVP_EINVAL;
+    size_t off = 0, len = 0;
+    const size_t n32 = 32 * (size_t)c->K, ns = c->cfg.n_samples;
+    switch (what) {
+        case HVP_OUT_T: off = c->off_T(); len = 2 * ns; break;
+        case HVP_OUT_OMEGA: off = c->off_Om(); len = 2 * ns; break;
+        case HVP_OUT_GRAD_E: off = c->off_ge(); len = n32; break;
+        case HVP_OUT_HVP_E: off = c->off_he(); len = n32; break;
+        case HVP_OUT_GRAD_R: off = c->off_gr(); len = n32; break;
+        case HVP_OUT_HVP_R: off = c->off_hr(); len = n32; break;
+        case HVP_OUT_LOSS: off = 0; len = 1; break;
+        case HVP_OUT_ENV:
+            CUDA_TRY(c, cudaMemcpyAsync(out, c->d_env, sizeof(double) * 64 * c->K * ns, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            return HVP_OK;
+        default: return fail(c, HVP_EINVAL, "unknown output selector");
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->d_res + off, sizeof(double) * len, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return HVP_OK;
+}
+
+int hvp_plan_info(const hvp_ctx* c, long long info[8]) {
+    if (!c || !info) return HVP_EINVAL;
+    info[0] = c->K;
+    info[1] = c->unfused ? c->K : c->P;
+    info[2] = c->w;
+    info[3] = c->stride;
+    info[4] = c->launches_per_call[1];
+    info[5] = (long long)(c->bytes >> 20);
+    info[6] = c->tiles_per_cta;
+    info[7] = c->cx_count;
+    return HVP_OK;
+}
+
+void hvp_free(hvp_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& g : c->gexec)
+        if (g) cudaGraphExecDestroy(g);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_in) cudaFreeHost(c->h_in);
+    if (c->h_res) cudaFreeHost(c->h_res);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* hvp_last_error(const hvp_ctx* c) {
+    if (c) return c->err.c_str();
+    return g_init_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Internal declarations shared by the translation units of libhvp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+namespace hvp {
+
+constexpr int kMaxN = 30;            // qubits
+constexpr int kMaxW = 14;            // local qubits per shared-memory tile
+constexpr int kMaxGatesPerPass = 64; // shared-memory budget of one window pass
+constexpr int kLowBits = 4;          // address bits every tile keeps contiguous (16 amplitudes)
+
+// ----------------------------------------------------------------- host plan
+
+// One window pass: all gates whose two qubits lie in the window S and whose
+// predecessors are done, applied to every tile of 2^|S| amplitudes.
+struct PassPlan {
+    std::vector<int> S;        // window qubits; shared-memory index bit j <-> qubit S[j]
+    std::vector<int> gates;    // gate indices, in an order that respects the circuit
+    std::vector<int> pos_in;   // qubit -> amplitude-index bit before the pass
+    std::vector<int> pos_out;  // qubit -> amplitude-index bit after the pass
+};
+
+struct Plan {
+    int n = 0, L = 0, K = 0, w = 0, b = 0;
+    std::vector<int> first_qubit;   // gate k acts on (first_qubit[k], first_qubit[k] + 1)
+    std::vector<PassPlan> passes;
+    std::vector<int> pass_of_gate;
+};
+
+int num_gates(int n, int L);
+void brickwall_layout(int n, int L, std::vector<int>& first_qubit);
+// Returns 0 or a negative HVP_* code.
+int make_plan(int n, int L, int w, int b, Plan& plan);
+// Per-gate passes (the unfused schedule): one pass per gate, standard layout.
+int make_unfused_plan(int n, int L, Plan& plan);
+
+// ------------------------------------------------------- device descriptors
+
+// Address and shared-memory index tables of one pass. "Address rank" m
+// enumerates the tile's 2^w amplitudes in increasing address order.
+struct DevPass {
+    int w;                  // local bits
+    int ng;                 // global bits (n - w)
+    int n_gates;
+    int gate_off;           // first entry in the DevGate array
+    int gpos[32];           // amplitude-index bit of global tile bit r
+    int gq[32];             // qubit at global tile bit r
+    int sq[16];             // qubit of shared-memory index bit j
+    uint32_t off_lo[64];    // address offset of rank bits [0, 6)
+    uint32_t off_hi[256];   // address offset of rank bits [6, w)
+    uint16_t in_lo[64], in_hi[256];    // shared-memory index of a rank, input layout
+    uint16_t out_lo[64], out_hi[256];  // the same for the output layout
+};
+
+struct DevGate {
+    int k;   // gate index
+    int u;   // shared-memory bit of qubit i (high bit of the 2-bit gate index)
+    int v;   // shared-memory bit of qubit i + 1
+    int pad;
+};
+
+void build_dev_passes(const Plan& plan, std::vector<DevPass>& dp, std::vector<DevGate>& dg);
+
+// Swizzle of shared-memory element indices (16-byte elements): conflict-free
+// 128-bit accesses when no two neighbouring qubits sit on index bits 0..2.
+__host__ __device__ inline unsigned swz(unsigned l) {
+    return l ^ ((((l >> 3) ^ (l >> 4)) & 1u) * 7u);
+}
+
+// ----------------------------------------------------------- kernel arguments
+
+enum PassMode : int {
+    M_GEN = 1,        // generate the product state psi^[0] instead of loading
+    M_FWD = 2,        // apply the pass's gates forward
+    M_STORE_F = 4,    // store the forward states
+    M_BWD = 8,        // apply the pass's gates backward with environment sums
+    M_LOAD_PHI = 16,  // co-states start as (phi, 0)
+    M_STORE_B = 32,   // store the co-states
+};
+
+struct Mats32 { float2 G[16], Ginv[16], Gh[16], V[16], Vh[16]; };
+struct Mats64 { double2 G[16], Ginv[16], Gh[16], V[16], Vh[16]; };
+
+struct TiledArgs {
+    const DevPass* pass;
+    const DevGate* gates;        // all gates of all passes
+    const Mats32* mats;          // K entries
+    const float2* psi1q;         // N_s x n x 2
+    const void* xin;             // forward states in (float4 or float2 per amplitude)
+    void* xout;                  // forward states out
+    const float2* phi;           // reference states
+    const void* cin;             // co-states in
+    void* cout;                  // co-states out
+    double* partial;             // [K][N_s][CX][64]
+    int n, n_samples, mode, tiles_per_cta, cx_count;
+    int ld_out_tab;              // 1: load through the output-layout tables
+    int st_out_tab;              // 1: store through the output-layout tables
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, int max_gates,
+                         cudaStream_t st);
+size_t tiled_smem_bytes(bool tangent, bool bwd, int w, int threads, int max_gates);
+cudaError_t tiled_set_smem_limits();
+
+template <typename R>
+struct UnfusedArgs;
+
+// Unfused (one launch per gate) kernels, real type R = float or double.
+cudaError_t unfused_init(bool dbl, const void* psi1q, void* x, int n, int ns, bool tangent, cudaStream_t st);
+cudaError_t unfused_fwd_gate(bool dbl, const void* mats, int k, int q, void* x, int n, int ns,
+                             bool tangent, cudaStream_t st);
+cudaError_t unfused_load_phi(bool dbl, const void* phi, void* c, int n, int ns, bool tangent, cudaStream_t st);
+cudaError_t unfused_bwd_gate(bool dbl, const void* mats, int k, int q, void* x, void* c, double* partial,
+                             int n, int ns, int cx_count, bool tangent, cudaStream_t st);
+int unfused_cx_count(int n, int ns);
+
+// Post-processing (FP64).
+struct PostArgs {
+    const double* partial;  // [K][N_s][CX][64]
+    double* env;            // [N_s][K][64]
+    const double2* G;       // K x 16
+    const double2* V;       // K x 16 (may be null)
+    double2* T;             // N_s
+    double2* Omega;         // N_s
+    double* loss;           // 1
+    double2* grad_e;        // K x 16
+    double2* hvp_e;
+    double2* grad_r;
+    double2* hvp_r;
+    int K, n_samples, cx_count, tangent;
+};
+cudaError_t launch_post(const PostArgs& p, cudaStream_t st);
+cudaError_t launch_prep(const double2* G, const double2* V, void* mats, bool dbl, int K, int* status,
+                        cudaStream_t st);
+cudaError_t launch_psi1q_convert(const double* in, float2* out, size_t count, cudaStream_t st);
+cudaError_t launch_phi_permute(const double2* phi_std, void* phi_out, bool dbl, int n, int ns,
+                               const int* pos, cudaStream_t st);
+cudaError_t launch_copy_out(const double* loss, const double2* grad, const double2* hvp,
+                            double* loss_dst, double* grad_dst, double* hvp_dst, int K,
+                            cudaStream_t st);
+
+}  // namespace hvp

@@ -1,0 +1,191 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (the bar of the benchmark plan): complex64 sweeps with FP64
+accumulation within 1e-5 relative (Frobenius norm over all K blocks) for the
+gradient and the HVP; the complex128 path within 1e-11. The loss is compared
+as the mean fidelity F = 1 - C relatively (C is within 2^-n of 1 for random
+circuits) and as C absolutely.
+"""
+import numpy as np
+import pytest
+
+from common import rel
+from oracle import oracle
+from paper_2604_20384_gb300 import native
+from paper_2604_20384_gb300.inputs import make_workload, random_direction
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-5, "c128": 1e-11}
+
+
+def _oracle(w, G=None, V=None, phi=None, want_env=False):
+    if phi is None:
+        phi = oracle.reference_states(w.n, w.n_layers, w.Uref, w.psi1q)
+    o = oracle.evaluate(w.n, w.n_layers, w.G if G is None else G, w.V if V is None else V, w.psi1q, phi,
+                        want_env=want_env)
+    return o, phi
+
+
+def _check(ctx, w, o, tol, G=None, V=None):
+    loss, grad, hvp = ctx.hvp(w.G if G is None else G, w.V if V is None else V)
+    F, Fo = 1 - loss, 1 - o["loss"]
+    assert abs(F - Fo) <= tol * abs(Fo) + 1e-13, (F, Fo)
+    assert abs(loss - o["loss"]) <= max(tol, 1e-13)
+    key_g, key_h = ("grad_r", "hvp_r") if ctx.riemannian else ("grad", "hvp")
+    assert rel(grad, o[key_g]) < tol, rel(grad, o[key_g])
+    assert rel(hvp, o[key_h]) < tol, rel(hvp, o[key_h])
+    assert rel(ctx.get("T"), o["T"]) < tol
+    assert rel(ctx.get("Omega"), o["Omega"]) < tol
+    assert rel(ctx.get("grad_e"), o["grad"]) < tol
+    assert rel(ctx.get("hvp_e"), o["hvp"]) < tol
+    assert rel(ctx.get("grad_r"), o["grad_r"]) < tol
+    assert rel(ctx.get("hvp_r"), o["hvp_r"]) < tol
+    return loss, grad, hvp
+
+
+@pytest.mark.parametrize("precision,unfused", [("c128", True), ("c64", False), ("c64", True)])
+def test_small_brickwall_all_paths(precision, unfused):
+    w = make_workload(6, 3, 16, seed=0)
+    o, phi = _oracle(w)
+    with native.Context(6, 3, w.psi1q, w.Uref, precision=precision, unfused=unfused) as ctx:
+        _check(ctx, w, o, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_n12_precision_comparison(precision):
+    w = make_workload(12, 8, 256, seed=0)
+    o, phi = _oracle(w)
+    with native.Context(12, 8, w.psi1q, w.Uref, precision=precision) as ctx:
+        _check(ctx, w, o, TOL[precision])
+
+
+@pytest.mark.parametrize("n,L,ns,window", [(14, 7, 5, 10), (16, 9, 3, 12), (13, 11, 7, 8), (15, 6, 2, 9),
+                                           (10, 12, 9, 6)])
+def test_multi_pass_tiles_with_ragged_shapes(n, L, ns, window):
+    # several passes, several tiles per sample, layouts permuted between passes
+    w = make_workload(n, L, ns, seed=n + L)
+    o, phi = _oracle(w)
+    with native.Context(n, L, w.psi1q, w.Uref, window=window) as ctx:
+        assert ctx.plan_info()["passes"] > 1
+        _check(ctx, w, o, TOL["c64"])
+
+
+def test_loss_and_gradient_only_call():
+    w = make_workload(14, 6, 4, seed=3)
+    o, phi = _oracle(w)
+    for prec, unf in (("c64", False), ("c128", True)):
+        with native.Context(14, 6, w.psi1q, w.Uref, precision=prec, unfused=unf, window=10) as ctx:
+            loss, grad = ctx.loss_grad(w.G)
+            assert abs(loss - o["loss"]) <= TOL[prec]
+            assert rel(grad, o["grad"]) < TOL[prec]
+            assert rel(ctx.get("T"), o["T"]) < TOL[prec]
+
+
+def test_riemannian_outputs_and_near_solution():
+    w = make_workload(13, 6, 8, seed=5, near_solution=0.1)
+    o, phi = _oracle(w)
+    assert np.min(np.abs(o["T"])) > 0.3
+    with native.Context(13, 6, w.psi1q, w.Uref, riemannian=True, window=10) as ctx:
+        _check(ctx, w, o, TOL["c64"])
+
+
+def test_phi_given_and_non_unitary_gates():
+    w = make_workload(11, 5, 6, seed=8)
+    rng = np.random.default_rng(1)
+    Gn = w.G + 0.05 * (rng.standard_normal(w.G.shape) + 1j * rng.standard_normal(w.G.shape))
+    o, phi = _oracle(w, G=Gn)
+    for prec in ("c64", "c128"):
+        with native.Context(11, 5, w.psi1q, phi, phi_given=True, precision=prec, window=8) as ctx:
+            _check(ctx, w, o, TOL[prec], G=Gn)
+
+
+def test_single_gate_and_single_sample():
+    w = make_workload(2, 1, 1, seed=4)
+    o, phi = _oracle(w)
+    for prec in ("c64", "c128"):
+        with native.Context(2, 1, w.psi1q, w.Uref, precision=prec) as ctx:
+            _check(ctx, w, o, TOL[prec])
+
+
+def test_checkpoint_stride_graphs_and_repeat_calls_are_bit_identical():
+    w = make_workload(16, 14, 4, seed=9)
+    o, phi = _oracle(w)
+    results = []
+    for stride, graphs in ((1, True), (2, True), (3, False), (100, True)):
+        with native.Context(16, 14, w.psi1q, w.Uref, window=9, checkpoint_stride=stride, graphs=graphs) as ctx:
+            info = ctx.plan_info()
+            assert info["passes"] >= 4
+            r1 = ctx.hvp(w.G, w.V)
+            r2 = ctx.hvp(w.G, w.V)
+            assert r1[0] == r2[0] and np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+            results.append(r1)
+    for r in results[1:]:
+        assert r[0] == results[0][0] and np.array_equal(r[1], results[0][1]) and np.array_equal(r[2], results[0][2])
+    assert rel(results[0][2], o["hvp"]) < TOL["c64"]
+
+
+def test_per_sample_environments_match_oracle():
+    w = make_workload(12, 5, 3, seed=12)
+    o, phi = _oracle(w, want_env=True)
+    with native.Context(12, 5, w.psi1q, w.Uref, window=8) as ctx:
+        ctx.hvp(w.G, w.V)
+        E, DE = ctx.get("env")
+    assert rel(E, o["E"]) < TOL["c64"]
+    assert rel(DE, o["DE"]) < TOL["c64"]
+
+
+def test_hvp_symmetry_on_gpu():
+    w = make_workload(12, 6, 8, seed=21)
+    W = random_direction(w.K, w.G, seed=5)
+    with native.Context(12, 6, w.psi1q, w.Uref) as ctx:
+        hv = ctx.hvp(w.G, w.V)[2]
+        hw = ctx.hvp(w.G, W)[2]
+    a = np.real(np.vdot(W.ravel(), hv.ravel()))
+    b = np.real(np.vdot(w.V.ravel(), hw.ravel()))
+    assert abs(a - b) < 1e-5 * max(abs(a), 1e-3)
+
+
+def test_errors_are_reported_not_raised_on_device():
+    w = make_workload(8, 3, 2, seed=2)
+    with native.Context(8, 3, w.psi1q, w.Uref) as ctx:
+        G = w.G.copy()
+        G[1] = 0.0                               # singular gate: no inverse
+        with pytest.raises(native.HVPError) as e:
+            ctx.hvp(G, w.V)
+        assert e.value.code == native.HVP_ENONFINITE
+        G = w.G.copy()
+        G[0, 0, 0] = np.nan
+        with pytest.raises(native.HVPError) as e:
+            ctx.loss_grad(G)
+        assert e.value.code == native.HVP_ENONFINITE
+        # the context stays usable
+        o, phi = _oracle(w)
+        _check(ctx, w, o, TOL["c64"])
+
+
+def test_headline_shape_sampled_against_oracle():
+    # n = 20, L = 16, N_s = 64 in the benchmark's launch configuration; the
+    # oracle checks two of the samples one by one (T_s, Omega_s and every
+    # per-sample environment), and the sample-summed outputs are checked
+    # through linearity in the samples.
+    w = make_workload(20, 16, 64, seed=0)
+    with native.Context(20, 16, w.psi1q, w.Uref) as ctx:
+        assert ctx.plan_info()["passes"] == 5
+        loss, grad, hvp = ctx.hvp(w.G, w.V)
+        T, Om = ctx.get("T"), ctx.get("Omega")
+        E, DE = ctx.get("env")
+    pick = [0, 37]
+    sub = w.psi1q[pick]
+    phi = oracle.reference_states(20, 16, w.Uref, sub)
+    o = oracle.evaluate(20, 16, w.G, w.V, sub, phi, threads=2, ckpt_stride=12, want_env=True)
+    assert rel(T[pick], o["T"]) < TOL["c64"]
+    assert rel(Om[pick], o["Omega"]) < TOL["c64"]
+    for i, s in enumerate(pick):
+        assert rel(E[s], o["E"][i]) < TOL["c64"]
+        assert rel(DE[s], o["DE"][i]) < TOL["c64"]
+    # sample sums from the per-sample pieces (Alg. 2 is linear in them)
+    g = -(2 / 64) * np.einsum("s,skij->kij", T, E.conj())
+    h = -(2 / 64) * (np.einsum("s,skij->kij", Om, E.conj()) + np.einsum("s,skij->kij", T, DE.conj()))
+    assert rel(grad, g) < 1e-9 and rel(hvp, h) < 1e-9
+    assert abs(loss - (1 - np.mean(np.abs(T) ** 2))) < 1e-12
