@@ -151,6 +151,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the unfused FP64 comparison sweep")
+    ap.add_argument("--samples", type=int, default=64,
+                    help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the device-resident timing (for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -177,7 +181,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = make_workload(**WORKLOAD)
+    w = make_workload(**dict(WORKLOAD, n_samples=args.samples))
     stream = torch.cuda.Stream(device=dev)
     ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
                          stream=stream.cuda_stream)
@@ -221,6 +225,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * 1000.0 / ms
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "HVPs/s", "ms_per_step": ms,
+                              "n_samples": args.samples, "quick": True}), flush=True)
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
     # ------------------------------------------------ end to end (host API)
     Gh = w.G.view(np.float64).reshape(-1).copy()
