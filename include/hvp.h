@@ -173,6 +173,36 @@ int hvp_plan_brickwall(int n, int n_layers, int window, int low_bits, int *pass_
 int hvp_profile(hvp_ctx *ctx, const double *G_dev, const double *V_dev, int max_launches,
                 float *ms, int *kind, double *flops, double *bytes);
 
+/* Loss, gradient and HVP without any device allocation, for callers that
+ * cannot call cudaMalloc: code running inside a framework that owns the whole
+ * device pool through its own allocator, a CUDA-graph replay harness whose
+ * memory plan is frozen, or a host process under a strict memory budget. The
+ * paper has no counterpart; it is an engineering entry point.
+ *
+ * The work space is one static device array of HVP_NOALLOC_SCRATCH_BYTES that
+ * every GPU which loads this library holds until the process exits. The
+ * caller passes all inputs and outputs as device pointers:
+ *   psi_1q_dev : N_s*n*4 doubles (as for hvp_init), phi_dev : the reference
+ *   states phi_s = U_ref psi_s, N_s * 2^n * 2 doubles in the standard layout;
+ *   G_dev, V_dev : K*32 doubles (V_dev NULL: loss and gradient only);
+ *   loss_dev (1 double), grad_dev, hvp_dev (K*32 doubles): Euclidean forms;
+ *   stream : cudaStream_t (NULL = legacy default stream).
+ * Limits: 2 <= n <= 12 (one 2^n tile per sample), K <= 64 gates, and a work
+ * space of 2^n*N_s*8 + K*N_s*1024 + K*1680 + N_s*(16n + 32) bytes plus at
+ * most 8 kB of tables and alignment, which must fit in
+ * HVP_NOALLOC_SCRATCH_BYTES (16 MiB; e.g. n = 12, L = 8, N_s = 128 fits);
+ * larger problems return HVP_EINVAL with a message in hvp_last_error(NULL). HVP_ENONFINITE reports a singular or
+ * non-finite gate. The call waits for its own work (it reads back a status
+ * word).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture. Every call reuses the same array, so
+ * calls that overlap on the GPU (other threads, other streams) race; serialise
+ * them. */
+#define HVP_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hvp_hvp_noalloc(int n, int n_layers, int n_samples, const double *psi_1q_dev,
+                    const double *phi_dev, const double *G_dev, const double *V_dev,
+                    double *loss_dev, double *grad_dev, double *hvp_dev, void *stream);
+
 /* Releases the context and all its device memory; NULL is ignored. */
 void hvp_free(hvp_ctx *ctx);
 

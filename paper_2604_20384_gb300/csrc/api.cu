@@ -38,6 +38,11 @@ std::string fmt(const char* f, ...) {
 
 }  // namespace
 
+namespace hvp {
+// Message returned by hvp_last_error(NULL) on the calling thread.
+void set_thread_error(const char* msg) { g_init_error = msg; }
+}  // namespace hvp
+
 struct hvp_ctx {
     hvp_config cfg{};
     int K = 0;

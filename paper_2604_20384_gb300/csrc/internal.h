@@ -145,4 +145,6 @@ cudaError_t launch_copy_out(const double* loss, const double2* grad, const doubl
                             double* loss_dst, double* grad_dst, double* hvp_dst, int K,
                             cudaStream_t st);
 
+void set_thread_error(const char* msg);
+
 }  // namespace hvp

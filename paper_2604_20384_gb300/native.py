@@ -71,6 +71,8 @@ def load() -> ctypes.CDLL:
     lib.hvp_profile.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                 ctypes.POINTER(ctypes.c_int), _dp, _dp]
     lib.hvp_profile.restype = ctypes.c_int
+    lib.hvp_hvp_noalloc.argtypes = [ctypes.c_int] * 3 + [vp] * 8
+    lib.hvp_hvp_noalloc.restype = ctypes.c_int
     lib.hvp_free.argtypes = [vp]
     lib.hvp_free.restype = None
     lib.hvp_last_error.argtypes = [vp]
@@ -99,6 +101,21 @@ def plan_brickwall(n: int, n_layers: int, window: int = 12, low_bits: int = 4):
     if P < 0:
         raise HVPError(P, "hvp_plan_brickwall failed")
     return P, np.array(arr[:K], dtype=np.int64)
+
+
+def hvp_noalloc(n: int, n_layers: int, n_samples: int, psi1q_ptr: int, phi_ptr: int, G_ptr: int,
+                V_ptr: int | None, loss_ptr: int | None, grad_ptr: int | None, hvp_ptr: int | None,
+                stream: int | None = None) -> None:
+    """Loss, gradient and HVP on device pointers without any device allocation
+    (hvp_hvp_noalloc): for callers whose memory is owned by someone else, e.g.
+    a framework allocator holding the whole device pool or a frozen memory
+    plan. Work space is a fixed 16 MiB static device array shared by all calls
+    on a device, so calls must not overlap on the GPU."""
+    lib = load()
+    rc = lib.hvp_hvp_noalloc(n, n_layers, n_samples, psi1q_ptr, phi_ptr, G_ptr, V_ptr, loss_ptr, grad_ptr,
+                             hvp_ptr, stream)
+    if rc != HVP_OK:
+        raise HVPError(rc, lib.hvp_last_error(None).decode())
 
 
 def _f64(a, shape_last=None):
