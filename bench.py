@@ -153,6 +153,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the unfused FP64 comparison sweep")
     ap.add_argument("--samples", type=int, default=64,
                     help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
+    ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
+    ap.add_argument("--variant", type=int, default=0, help="1 scalar FMA, 2 packed FMA (0 = library default)")
+    ap.add_argument("--window", type=int, default=0, help="window qubits (0 = library default)")
+    ap.add_argument("--autotune", action="store_true", help="let the library autotune at set-up")
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (for profiler captures)")
     args = ap.parse_args()
@@ -184,7 +188,8 @@ def main():
     w = make_workload(**dict(WORKLOAD, n_samples=args.samples))
     stream = torch.cuda.Stream(device=dev)
     ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
-                         stream=stream.cuda_stream)
+                         stream=stream.cuda_stream, threads=args.threads, variant=args.variant,
+                         window=args.window, autotune=args.autotune)
     K = w.K
     G_dev = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
     V_dev = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
@@ -228,7 +233,8 @@ def main():
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "HVPs/s", "ms_per_step": ms,
-                              "n_samples": args.samples, "quick": True}), flush=True)
+                              "n_samples": args.samples, "quick": True, "plan": info, "clocks": clocks}),
+                  flush=True)
         ctx.close()
         if dist:
             dist.destroy_process_group()

@@ -61,6 +61,8 @@ extern "C" {
 #define HVP_PHI_GIVEN 2   /* ref_data holds phi_s (N_s x 2^n) instead of U_ref */
 #define HVP_UNFUSED 4     /* one kernel launch per gate (the plain schedule)    */
 #define HVP_NO_GRAPH 8    /* launch kernels directly instead of a CUDA graph   */
+#define HVP_AUTOTUNE 16   /* time the window/threads/arithmetic candidates at
+                             hvp_init and keep the fastest (see hvp_plan_info) */
 
 typedef struct hvp_ctx hvp_ctx;
 
@@ -73,6 +75,10 @@ typedef struct {
     int checkpoint_stride; /* forward checkpoints every this many window
                               passes, the others recomputed; 0 = automatic     */
     int window;            /* local qubits per shared-memory tile; 0 = auto    */
+    int threads;           /* threads per CTA of the window-pass kernels,
+                              256 or 512; 0 = auto                             */
+    int variant;           /* arithmetic of the window-pass kernels: 1 scalar
+                              FP32 FMA, 2 packed fma.rn.f32x2; 0 = auto        */
     int device;            /* CUDA device ordinal                              */
     void *stream;          /* cudaStream_t for all work; NULL = own stream     */
 } hvp_config;
@@ -140,8 +146,9 @@ int hvp_get(hvp_ctx *ctx, int what, double *out);
  *   info[0] = K, info[1] = number of window passes P, info[2] = window
  *   (local qubits per tile), info[3] = checkpoint stride, info[4] = kernel
  *   launches of the last hvp call, info[5] = device memory held by the
- *   context in MiB, info[6] = tiles per CTA, info[7] = CTAs per sample. */
-int hvp_plan_info(const hvp_ctx *ctx, long long info[8]);
+ *   context in MiB, info[6] = tiles per CTA, info[7] = CTAs per sample,
+ *   info[8] = threads per CTA, info[9] = arithmetic variant. */
+int hvp_plan_info(const hvp_ctx *ctx, long long info[10]);
 
 /* Window-pass plan of a brickwall without a context or GPU (for tests and
  * tools): fills pass_of_gate[K] with the pass index of each gate and returns

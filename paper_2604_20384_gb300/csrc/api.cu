@@ -48,7 +48,7 @@ struct hvp_ctx {
     int K = 0;
     bool dbl = false, unfused = false;
     Plan plan;
-    int w = 0, threads = 256, tiles_per_cta = 1, cx_count = 1, stride = 1, P = 0, max_gates = 0;
+    int w = 0, threads = 256, variant = 1, tiles_per_cta = 1, cx_count = 1, stride = 1, P = 0, max_gates = 0;
     int n_slots = 0, s0_last = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -172,7 +172,7 @@ int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool ta
     a.ld_out_tab = ld_out;
     a.st_out_tab = st_out;
     const int ng = (int)c->plan.passes[p].gates.size();
-    CUDA_TRY(c, launch_tiled(a, tan, c->w, c->threads, std::max(ng, 1), c->stream));
+    CUDA_TRY(c, launch_tiled(a, tan, c->w, c->threads, std::max(ng, 1), c->stream, c->variant));
     if (c->prof) {
         // Algorithmic work: 12 (36) complex MACs per amplitude per gate forward
         // (backward) with tangents, 4 (12) without; 8 flops per complex MAC.
@@ -364,11 +364,14 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (L < 1) return fail(c, HVP_EINVAL, "n_layers must be >= 1");
     if (ns < 1) return fail(c, HVP_EINVAL, "n_samples must be >= 1");
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
-    if (cfg->flags & ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH))
+    if (cfg->flags & ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE))
         return fail(c, HVP_EINVAL, "unknown flag bits");
     if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
     if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))
         return fail(c, HVP_EINVAL, "window must be 0 (auto) or in [6, 12]");
+    if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
+        return fail(c, HVP_EINVAL, "threads must be 0 (auto), 256 or 512");
+    if (cfg->variant < 0 || cfg->variant > 2) return fail(c, HVP_EINVAL, "variant must be 0 (auto), 1 or 2");
     if (((size_t)1 << n) * (size_t)ns > ((size_t)1 << 34))
         return fail(c, HVP_EINVAL, "2^n * n_samples above 2^34 amplitudes");
     if (!all_finite(psi_1q, (size_t)ns * n * 4)) return fail(c, HVP_ENONFINITE, "psi_1q is not finite");
@@ -400,6 +403,8 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     } else {
         CUDA_TRY(c, tiled_set_smem_limits());
         c->w = std::min(n, cfg->window ? cfg->window : 12);
+        c->threads = cfg->threads ? cfg->threads : 256;
+        c->variant = cfg->variant ? cfg->variant : 1;
         if ((rc = make_plan(n, L, c->w, std::min(kLowBits, c->w - 1), c->plan))) return fail(c, rc, "planning failed");
         c->P = (int)c->plan.passes.size();
         for (auto& pp : c->plan.passes) c->max_gates = std::max(c->max_gates, (int)pp.gates.size());
@@ -640,7 +645,7 @@ int hvp_get(hvp_ctx* c, int what, double* out) {
     return HVP_OK;
 }
 
-int hvp_plan_info(const hvp_ctx* c, long long info[8]) {
+int hvp_plan_info(const hvp_ctx* c, long long info[10]) {
     if (!c || !info) return HVP_EINVAL;
     info[0] = c->K;
     info[1] = c->unfused ? c->K : c->P;
@@ -650,6 +655,8 @@ int hvp_plan_info(const hvp_ctx* c, long long info[8]) {
     info[5] = (long long)(c->bytes >> 20);
     info[6] = c->tiles_per_cta;
     info[7] = c->cx_count;
+    info[8] = c->threads;
+    info[9] = c->variant;
     return HVP_OK;
 }
 

@@ -36,8 +36,6 @@ int num_gates(int n, int L);
 void brickwall_layout(int n, int L, std::vector<int>& first_qubit);
 // Returns 0 or a negative HVP_* code.
 int make_plan(int n, int L, int w, int b, Plan& plan);
-// Per-gate passes (the unfused schedule): one pass per gate, standard layout.
-int make_unfused_plan(int n, int L, Plan& plan);
 
 // ------------------------------------------------------- device descriptors
 
@@ -103,13 +101,11 @@ struct TiledArgs {
 };
 
 // Launchers (return cudaError_t of the launch).
+// variant 1: scalar FP32 FMAs; 2: packed fma.rn.f32x2. threads: 256 or 512.
 cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, int max_gates,
-                         cudaStream_t st);
-size_t tiled_smem_bytes(bool tangent, bool bwd, int w, int threads, int max_gates);
+                         cudaStream_t st, int variant = 1);
+size_t tiled_smem_bytes(bool tangent, int mode, int w, int threads, int max_gates, int variant = 1);
 cudaError_t tiled_set_smem_limits();
-
-template <typename R>
-struct UnfusedArgs;
 
 // Unfused (one launch per gate) kernels, real type R = float or double.
 cudaError_t unfused_init(bool dbl, const void* psi1q, void* x, int n, int ns, bool tangent, cudaStream_t st);

@@ -1,4 +1,4 @@
-// Window-pass kernel of the complex64 sweep (sm_103a).
+// Window-pass kernels of the complex64 sweep (sm_103a).
 //
 // One CTA owns tiles of 2^w amplitudes (the w window qubits vary, the other
 // n - w qubits are fixed) of one sample. It loads the tile's forward states
@@ -19,49 +19,102 @@
 // boundaries it comes from the forward checkpoint, so recomputation error does
 // not build up over the whole circuit.
 //
+// Two kernels: a forward-only kernel (small register footprint, two CTAs per
+// SM) and a backward kernel (forward part of the turnaround pass included).
+// Two arithmetic forms, chosen at run time: scalar FP32 FMAs, or packed
+// fma.rn.f32x2 with gate matrices pre-expanded to {m.re, m.re, -m.im, m.im}
+// so that one complex multiply-add is two packed FMAs.
+//
 // Environment sums: per thread in FP32 over its groups of four amplitudes,
 // a warp reduce-scatter (each lane ends with two of the 64 real components),
-// a cross-warp sum in FP64 in shared memory, and one FP64 record per
-// (gate, sample, CTA) in global memory.
-#include <type_traits>
-
+// a cross-warp FP32 sum per gate into a per-CTA FP32 accumulator, and one
+// FP64 record per (gate, sample, CTA) in global memory at the end.
 #include "internal.h"
 
 namespace hvp {
 
 namespace {
 
-__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {  // acc += a b
-    acc.x = fmaf(a.x, b.x, acc.x);
-    acc.x = fmaf(-a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y);
-    acc.y = fmaf(a.y, b.x, acc.y);
-}
-
-__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {  // acc += conj(a) b
-    acc.x = fmaf(a.x, b.x, acc.x);
-    acc.x = fmaf(a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y);
-    acc.y = fmaf(-a.y, b.x, acc.y);
+__device__ __forceinline__ unsigned insert0(unsigned x, int p) {
+    return ((x >> p) << (p + 1)) | (x & ((1u << p) - 1u));
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ unsigned insert0(unsigned x, int p) {
-    return ((x >> p) << (p + 1)) | (x & ((1u << p) - 1u));
-}
+__device__ __forceinline__ float2 swp(float2 x) { return make_float2(x.y, x.x); }
+
+// ---------------------------------------------------------------- arithmetic
+// Matrix element storage: scalar form keeps float2 {re, im}; packed form keeps
+// float4 {re, re, -im, im} so that acc += m x is
+//     acc = fma2({re, re}, {x.re, x.im}, acc); acc = fma2({-im, im}, {x.im, x.re}, acc).
+template <bool P2>
+struct Math;
+
+template <>
+struct Math<false> {
+    using M = float2;
+    static constexpr int kMatBytes = 8;
+    __device__ static __forceinline__ void mac(float2& acc, const M& m, float2 x, float2 /*xs*/) {
+        acc.x = fmaf(m.x, x.x, acc.x);
+        acc.x = fmaf(-m.y, x.y, acc.x);
+        acc.y = fmaf(m.x, x.y, acc.y);
+        acc.y = fmaf(m.y, x.x, acc.y);
+    }
+    __device__ static __forceinline__ void msub(float2& acc, const M& m, float2 x, float2 /*xs*/) {  // acc -= m x
+        acc.x = fmaf(-m.x, x.x, acc.x);
+        acc.x = fmaf(m.y, x.y, acc.x);
+        acc.y = fmaf(-m.x, x.y, acc.y);
+        acc.y = fmaf(-m.y, x.x, acc.y);
+    }
+    // acc += conj(a) x; (ar, ai) = a as given, x and its swap
+    __device__ static __forceinline__ void cmac(float2& acc, float2 a, float2 x, float2 /*xs*/) {
+        acc.x = fmaf(a.x, x.x, acc.x);
+        acc.x = fmaf(a.y, x.y, acc.x);
+        acc.y = fmaf(a.x, x.y, acc.y);
+        acc.y = fmaf(-a.y, x.x, acc.y);
+    }
+    __device__ static __forceinline__ M expand(float2 m) { return m; }
+};
+
+template <>
+struct Math<true> {
+    using M = float4;
+    static constexpr int kMatBytes = 16;
+    __device__ static __forceinline__ void mac(float2& acc, const M& m, float2 x, float2 xs) {
+        acc = __ffma2_rn(make_float2(m.x, m.y), x, acc);
+        acc = __ffma2_rn(make_float2(m.z, m.w), xs, acc);
+    }
+    __device__ static __forceinline__ void msub(float2& acc, const M& m, float2 x, float2 xs) {
+        acc = __ffma2_rn(make_float2(-m.x, -m.y), x, acc);
+        acc = __ffma2_rn(make_float2(-m.z, -m.w), xs, acc);
+    }
+    // acc += conj(a) x = {a.re, a.re} x + {a.im, -a.im} swap(x)
+    __device__ static __forceinline__ void cmac(float2& acc, float2 a, float2 x, float2 xs) {
+        acc = __ffma2_rn(make_float2(a.x, a.x), x, acc);
+        acc = __ffma2_rn(make_float2(a.y, -a.y), xs, acc);
+    }
+    __device__ static __forceinline__ M expand(float2 m) { return make_float4(m.x, m.x, -m.y, m.y); }
+};
 
 // y = M x for a 4x4 complex matrix in shared memory (row-major).
-__device__ __forceinline__ void matvec4(const float2* __restrict__ M, const float2 (&x)[4], float2 (&y)[4]) {
+template <bool P2>
+__device__ __forceinline__ void matvec4(const typename Math<P2>::M* __restrict__ M, const float2 (&x)[4],
+                                        const float2 (&xs)[4], float2 (&y)[4]) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) cmac(acc, M[r * 4 + c], x[c]);
+        for (int c = 0; c < 4; ++c) Math<P2>::mac(acc, M[r * 4 + c], x[c], xs[c]);
         y[r] = acc;
     }
+}
+
+template <bool P2>
+__device__ __forceinline__ void swaps(const float2 (&x)[4], float2 (&xs)[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) xs[c] = P2 ? swp(x[c]) : x[c];
 }
 
 // Reduce-scatter of NV values over a warp: afterwards lane l holds in v[0..NV/32)
@@ -92,11 +145,152 @@ struct Elt<false> { using T = float2; };
 __device__ __forceinline__ float2 lo2(float4 x) { return make_float2(x.x, x.y); }
 __device__ __forceinline__ float2 hi2(float4 x) { return make_float2(x.z, x.w); }
 
+// Matrix slots per gate in shared memory: forward kernel {G, V}; backward
+// kernel {G^-1, G^dag, V, V^dag} and, in the turnaround pass, also G.
+constexpr int kFwdMats = 2;
+
+// ------------------------------------------------------------ tile I/O
+struct TileCtx {
+    size_t base;
+    const uint32_t* offlo;
+    const uint32_t* offhi;
+};
+
+__device__ __forceinline__ size_t tile_base(const DevPass* __restrict__ P, unsigned t, size_t sample_off, int ng) {
+    size_t base = sample_off;
+    for (int r = 0; r < ng; ++r)
+        if ((t >> r) & 1u) base |= (size_t)1 << __ldg(&P->gpos[r]);
+    return base;
+}
+
+template <typename E, int NT>
+__device__ __forceinline__ void load_tile(E* __restrict__ dst, const E* __restrict__ src, const TileCtx& tc,
+                                          const uint16_t* lo, const uint16_t* hi, int Lt) {
+    for (int m = threadIdx.x; m < Lt; m += NT) {
+        const size_t addr = tc.base + __ldg(&tc.offlo[m & 63]) + __ldg(&tc.offhi[m >> 6]);
+        const unsigned l = __ldg(&lo[m & 63]) | __ldg(&hi[m >> 6]);
+        dst[swz(l)] = src[addr];
+    }
+}
+
+template <typename E, int NT>
+__device__ __forceinline__ void store_tile(E* __restrict__ dst, const E* __restrict__ src, const TileCtx& tc,
+                                           const uint16_t* lo, const uint16_t* hi, int Lt) {
+    for (int m = threadIdx.x; m < Lt; m += NT) {
+        const size_t addr = tc.base + __ldg(&tc.offlo[m & 63]) + __ldg(&tc.offhi[m >> 6]);
+        const unsigned l = __ldg(&lo[m & 63]) | __ldg(&hi[m >> 6]);
+        dst[addr] = src[swz(l)];
+    }
+}
+
+// psi^[0] = (x)_q psi_{s,q}: tile factor of the fixed qubits times the factors
+// of the window qubits (Eq. costHS, product states).
+template <typename E, int NT>
+__device__ __forceinline__ void gen_tile(E* __restrict__ sf, const DevPass* __restrict__ P, const float2* q1,
+                                         unsigned t, int w, int ng, int Lt) {
+    float2 gamma = make_float2(1.f, 0.f);
+    for (int r = 0; r < ng; ++r) gamma = cmulf(gamma, __ldg(&q1[2 * __ldg(&P->gq[r]) + ((t >> r) & 1u)]));
+    for (int l = threadIdx.x; l < Lt; l += NT) {
+        float2 amp = gamma;
+        for (int j = 0; j < w; ++j) amp = cmulf(amp, __ldg(&q1[2 * __ldg(&P->sq[j]) + ((l >> j) & 1)]));
+        if constexpr (sizeof(E) == 16) sf[swz(l)] = E{amp.x, amp.y, 0.f, 0.f};
+        else sf[swz(l)] = amp;
+    }
+}
+
+// Stage matrices of the pass's gates into shared memory (expanded for the
+// packed form): nmat slots per gate, slot i holding Mats32 field which[i]
+// (fields: 0 G, 1 G^-1, 2 G^dag, 3 V, 4 V^dag).
+template <bool P2, int NT>
+__device__ __forceinline__ void stage_mats(typename Math<P2>::M* __restrict__ dst, const TiledArgs& a, int goff,
+                                           int ngates, int nmat, const int* which) {
+    for (int i = threadIdx.x; i < ngates * nmat * 16; i += NT) {
+        const int g = i / (nmat * 16), rem = i - g * nmat * 16, mi = rem >> 4, e = rem & 15;
+        const int k = __ldg(&a.gates[goff + g].k);
+        const float2 v = reinterpret_cast<const float2*>(a.mats + k)[which[mi] * 16 + e];
+        dst[i] = Math<P2>::expand(v);
+    }
+}
+
+// One forward gate over all groups of the tile.
+template <bool TAN, bool P2, int NT>
+__device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, const typename Math<P2>::M* Gm,
+                                         const typename Math<P2>::M* Vm, int u, int v, int Lt) {
+    const int plo = min(u, v), phi_ = max(u, v);
+    const unsigned mu = 1u << u, mv = 1u << v;
+    for (int q = threadIdx.x; q < (Lt >> 2); q += NT) {
+        const unsigned l0 = insert0(insert0(q, plo), phi_);
+        const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
+        if constexpr (TAN) {
+            float2 p[4], d[4], ps[4], ds[4], np[4], nd[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { const float4 x = sf[idx[c]]; p[c] = lo2(x); d[c] = hi2(x); }
+            swaps<P2>(p, ps);
+            swaps<P2>(d, ds);
+            matvec4<P2>(Gm, p, ps, np);
+            matvec4<P2>(Gm, d, ds, nd);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Math<P2>::mac(nd[r], Vm[r * 4 + c], p[c], ps[c]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sf[idx[r]] = make_float4(np[r].x, np[r].y, nd[r].x, nd[r].y);
+        } else {
+            float2 p[4], ps[4], np[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[c] = sf[idx[c]];
+            swaps<P2>(p, ps);
+            matvec4<P2>(Gm, p, ps, np);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sf[idx[r]] = np[r];
+        }
+    }
+}
+
 }  // namespace
 
-template <bool TAN, int NT>
-__global__ void __launch_bounds__(NT, 1) tiled_pass_kernel(TiledArgs a) {
+// ------------------------------------------------------------ forward kernel
+template <bool TAN, bool P2, int NT>
+__global__ void __launch_bounds__(NT, 2) tiled_fwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
+    using MT = typename Math<P2>::M;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevPass* __restrict__ P = a.pass;
+    const int w = P->w, ng = P->ng, ngates = P->n_gates, goff = P->gate_off;
+    const int Lt = 1 << w;
+    const int s = blockIdx.y;
+    E* sf = reinterpret_cast<E*>(smem);
+    MT* mats = reinterpret_cast<MT*>(sf + Lt);
+    const int which[kFwdMats] = {0, 3};   // G, V
+    stage_mats<P2, NT>(mats, a, goff, ngates, kFwdMats, which);
+
+    const size_t sample_off = (size_t)s << a.n;
+    TileCtx tc{0, P->off_lo, P->off_hi};
+    const uint16_t* ldlo = a.ld_out_tab ? P->out_lo : P->in_lo;
+    const uint16_t* ldhi = a.ld_out_tab ? P->out_hi : P->in_hi;
+    const uint16_t* stlo = a.st_out_tab ? P->out_lo : P->in_lo;
+    const uint16_t* sthi = a.st_out_tab ? P->out_hi : P->in_hi;
+    for (int it = 0; it < a.tiles_per_cta; ++it) {
+        const unsigned t = blockIdx.x * a.tiles_per_cta + it;
+        tc.base = tile_base(P, t, sample_off, ng);
+        if (a.mode & M_GEN) gen_tile<E, NT>(sf, P, a.psi1q + (size_t)s * a.n * 2, t, w, ng, Lt);
+        else load_tile<E, NT>(sf, reinterpret_cast<const E*>(a.xin), tc, ldlo, ldhi, Lt);
+        __syncthreads();
+        for (int g = 0; g < ngates; ++g) {
+            const DevGate dg = a.gates[goff + g];
+            fwd_gate<TAN, P2, NT>(sf, mats + (g * kFwdMats) * 16, mats + (g * kFwdMats + 1) * 16, dg.u, dg.v, Lt);
+            __syncthreads();
+        }
+        if (a.mode & M_STORE_F) store_tile<E, NT>(reinterpret_cast<E*>(a.xout), sf, tc, stlo, sthi, Lt);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------- backward kernel
+template <bool TAN, bool P2, int NT>
+__global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
+    using E = typename Elt<TAN>::T;
+    using MT = typename Math<P2>::M;
     constexpr int NW = NT / 32;
     constexpr int NV = TAN ? 64 : 32;          // real components of one gate's sums
     extern __shared__ __align__(16) unsigned char smem[];
@@ -107,26 +301,20 @@ __global__ void __launch_bounds__(NT, 1) tiled_pass_kernel(TiledArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int s = blockIdx.y;
     const int mode = a.mode;
-    const bool bwd = (mode & M_BWD) != 0;
 
+    const int nmat = (mode & M_FWD) ? 5 : 4;
     E* sf = reinterpret_cast<E*>(smem);
     E* sb = sf + Lt;
-    float2* mats = reinterpret_cast<float2*>(sb + (bwd ? Lt : 0));
-    float* wred = reinterpret_cast<float*>(mats + ngates * 80);
-    double* acc = reinterpret_cast<double*>(wred + 2 * NW * 64);
+    MT* mats = reinterpret_cast<MT*>(sb + Lt);
+    float* wred = reinterpret_cast<float*>(mats + ngates * nmat * 16);
+    float* acc = wred + 2 * NW * 64;           // [ngates][NV] FP32 per CTA
 
-    // Gate matrices of this pass (G, G^-1, G^dag, V, V^dag per gate).
-    for (int i = tid; i < ngates * 80; i += NT) {
-        const int g = i / 80, e = i - g * 80;
-        const int k = __ldg(&a.gates[goff + g].k);
-        mats[i] = reinterpret_cast<const float2*>(a.mats + k)[e];
-    }
-    if (bwd)
-        for (int i = tid; i < ngates * NV; i += NT) acc[i] = 0.0;
+    const int which[5] = {1, 2, 3, 4, 0};      // G^-1, G^dag, V, V^dag, G
+    stage_mats<P2, NT>(mats, a, goff, ngates, nmat, which);
+    for (int i = tid; i < ngates * NV; i += NT) acc[i] = 0.f;
 
     const size_t sample_off = (size_t)s << a.n;
-    const uint32_t* offlo = P->off_lo;
-    const uint32_t* offhi = P->off_hi;
+    TileCtx tc{0, P->off_lo, P->off_hi};
     const uint16_t* ldlo = a.ld_out_tab ? P->out_lo : P->in_lo;
     const uint16_t* ldhi = a.ld_out_tab ? P->out_hi : P->in_hi;
     const uint16_t* stlo = a.st_out_tab ? P->out_lo : P->in_lo;
@@ -134,258 +322,206 @@ __global__ void __launch_bounds__(NT, 1) tiled_pass_kernel(TiledArgs a) {
 
     for (int it = 0; it < a.tiles_per_cta; ++it) {
         const unsigned t = blockIdx.x * a.tiles_per_cta + it;
-        size_t base = sample_off;
-        for (int r = 0; r < ng; ++r)
-            if ((t >> r) & 1u) base |= (size_t)1 << __ldg(&P->gpos[r]);
-
-        // ------------------------------------------------------------ load
-        if (mode & M_GEN) {
-            // psi^[0] = (x)_q psi_{s,q}: tile factor from the fixed qubits times
-            // the factors of the window qubits (Eq. costHS, product states).
-            const float2* q1 = a.psi1q + (size_t)s * a.n * 2;
-            float2 gamma = make_float2(1.f, 0.f);
-            for (int r = 0; r < ng; ++r) gamma = cmulf(gamma, __ldg(&q1[2 * __ldg(&P->gq[r]) + ((t >> r) & 1u)]));
-            for (int l = tid; l < Lt; l += NT) {
-                float2 amp = gamma;
-                for (int j = 0; j < w; ++j) amp = cmulf(amp, __ldg(&q1[2 * __ldg(&P->sq[j]) + ((l >> j) & 1)]));
-                if constexpr (TAN) sf[swz(l)] = make_float4(amp.x, amp.y, 0.f, 0.f);
-                else sf[swz(l)] = amp;
+        tc.base = tile_base(P, t, sample_off, ng);
+        if (mode & M_GEN) gen_tile<E, NT>(sf, P, a.psi1q + (size_t)s * a.n * 2, t, w, ng, Lt);
+        else load_tile<E, NT>(sf, reinterpret_cast<const E*>(a.xin), tc, ldlo, ldhi, Lt);
+        if (mode & M_LOAD_PHI) {
+            for (int m = tid; m < Lt; m += NT) {
+                const size_t addr = tc.base + __ldg(&tc.offlo[m & 63]) + __ldg(&tc.offhi[m >> 6]);
+                const unsigned l = __ldg(&ldlo[m & 63]) | __ldg(&ldhi[m >> 6]);
+                const float2 ph = a.phi[addr];
+                if constexpr (TAN) sb[swz(l)] = make_float4(ph.x, ph.y, 0.f, 0.f);
+                else sb[swz(l)] = ph;
             }
         } else {
-            const E* __restrict__ xin = reinterpret_cast<const E*>(a.xin);
-            for (int m = tid; m < Lt; m += NT) {
-                const size_t addr = base + __ldg(&offlo[m & 63]) + __ldg(&offhi[m >> 6]);
-                const unsigned l = __ldg(&ldlo[m & 63]) | __ldg(&ldhi[m >> 6]);
-                sf[swz(l)] = xin[addr];
-            }
-        }
-        if (bwd) {
-            if (mode & M_LOAD_PHI) {
-                for (int m = tid; m < Lt; m += NT) {
-                    const size_t addr = base + __ldg(&offlo[m & 63]) + __ldg(&offhi[m >> 6]);
-                    const unsigned l = __ldg(&ldlo[m & 63]) | __ldg(&ldhi[m >> 6]);
-                    const float2 ph = a.phi[addr];
-                    if constexpr (TAN) sb[swz(l)] = make_float4(ph.x, ph.y, 0.f, 0.f);
-                    else sb[swz(l)] = ph;
-                }
-            } else {
-                const E* __restrict__ cin = reinterpret_cast<const E*>(a.cin);
-                for (int m = tid; m < Lt; m += NT) {
-                    const size_t addr = base + __ldg(&offlo[m & 63]) + __ldg(&offhi[m >> 6]);
-                    const unsigned l = __ldg(&ldlo[m & 63]) | __ldg(&ldhi[m >> 6]);
-                    sb[swz(l)] = cin[addr];
-                }
-            }
+            load_tile<E, NT>(sb, reinterpret_cast<const E*>(a.cin), tc, ldlo, ldhi, Lt);
         }
         __syncthreads();
 
-        // --------------------------------------------------- forward gates
+        // Turnaround pass: forward through the gates first.
         if (mode & M_FWD) {
             for (int g = 0; g < ngates; ++g) {
                 const DevGate dg = a.gates[goff + g];
-                const float2* Gm = mats + g * 80;
-                const float2* Vm = Gm + 48;
-                const int u = dg.u, v = dg.v;
-                const int plo = min(u, v), phi_ = max(u, v);
-                const unsigned mu = 1u << u, mv = 1u << v;
-                for (int q = tid; q < (Lt >> 2); q += NT) {
-                    const unsigned l0 = insert0(insert0(q, plo), phi_);
-                    const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
-                    if constexpr (TAN) {
-                        float2 p[4], d[4], np[4], nd[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) { const float4 x = sf[idx[c]]; p[c] = lo2(x); d[c] = hi2(x); }
-                        matvec4(Gm, p, np);
-                        matvec4(Gm, d, nd);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) cmac(nd[r], Vm[r * 4 + c], p[c]);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) sf[idx[r]] = make_float4(np[r].x, np[r].y, nd[r].x, nd[r].y);
-                    } else {
-                        float2 p[4], np[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) p[c] = sf[idx[c]];
-                        matvec4(Gm, p, np);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) sf[idx[r]] = np[r];
-                    }
-                }
+                fwd_gate<TAN, P2, NT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 2) * 16, dg.u, dg.v, Lt);
                 __syncthreads();
             }
         }
 
-        // ------------------------------------------------------ store forward
-        if (mode & M_STORE_F) {
-            E* __restrict__ xout = reinterpret_cast<E*>(a.xout);
-            for (int m = tid; m < Lt; m += NT) {
-                const size_t addr = base + __ldg(&offlo[m & 63]) + __ldg(&offhi[m >> 6]);
-                const unsigned l = __ldg(&stlo[m & 63]) | __ldg(&sthi[m >> 6]);
-                xout[addr] = sf[swz(l)];
-            }
-        }
-
-        // -------------------------------------------------- backward gates
-        if (bwd) {
-            for (int g = ngates - 1; g >= 0; --g) {
-                const DevGate dg = a.gates[goff + g];
-                const float2* Gi = mats + g * 80 + 16;
-                const float2* Gh = mats + g * 80 + 32;
-                const float2* Vm = mats + g * 80 + 48;
-                const float2* Vh = mats + g * 80 + 64;
-                const int u = dg.u, v = dg.v;
-                const int plo = min(u, v), phi_ = max(u, v);
-                const unsigned mu = 1u << u, mv = 1u << v;
-                float red[NV];
+        for (int g = ngates - 1; g >= 0; --g) {
+            const DevGate dg = a.gates[goff + g];
+            const MT* Gi = mats + (g * nmat + 0) * 16;
+            const MT* Gh = mats + (g * nmat + 1) * 16;
+            const MT* Vm = mats + (g * nmat + 2) * 16;
+            const MT* Vh = mats + (g * nmat + 3) * 16;
+            const int u = dg.u, v = dg.v;
+            const int plo = min(u, v), phi_ = max(u, v);
+            const unsigned mu = 1u << u, mv = 1u << v;
+            float red[NV];
 #pragma unroll
-                for (int e = 0; e < NV; ++e) red[e] = 0.f;
-                for (int q = tid; q < (Lt >> 2); q += NT) {
-                    const unsigned l0 = insert0(insert0(q, plo), phi_);
-                    const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
-                    if constexpr (TAN) {
-                        float2 p[4], d[4], A[4], B[4], pp[4], tt[4], dp[4], nA[4], nB[4];
+            for (int e = 0; e < NV; ++e) red[e] = 0.f;
+            for (int q = tid; q < (Lt >> 2); q += NT) {
+                const unsigned l0 = insert0(insert0(q, plo), phi_);
+                const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
+                if constexpr (TAN) {
+                    float2 p[4], d[4], A[4], B[4], xs[4], pp[4], pps[4], tt[4], dp[4], dps[4], nA[4], nB[4];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float4 x = sf[idx[c]];
-                            const float4 y = sb[idx[c]];
-                            p[c] = lo2(x); d[c] = hi2(x); A[c] = lo2(y); B[c] = hi2(y);
-                        }
-                        matvec4(Gi, p, pp);                       // psi^[k-1]
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            tt[r] = d[r];
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const float2 vv = Vm[r * 4 + c];
-                                cmac(tt[r], make_float2(-vv.x, -vv.y), pp[c]);
-                            }
-                        }
-                        matvec4(Gi, tt, dp);                      // dpsi^[k-1]
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
-                                cmac_conj(e1, A[i], pp[j]);
-                                red[2 * (i * 4 + j)] = e1.x;
-                                red[2 * (i * 4 + j) + 1] = e1.y;
-                                float2 e2 = make_float2(red[32 + 2 * (i * 4 + j)], red[32 + 2 * (i * 4 + j) + 1]);
-                                cmac_conj(e2, B[i], pp[j]);
-                                cmac_conj(e2, A[i], dp[j]);
-                                red[32 + 2 * (i * 4 + j)] = e2.x;
-                                red[32 + 2 * (i * 4 + j) + 1] = e2.y;
-                            }
-                        matvec4(Gh, A, nA);
-                        matvec4(Gh, B, nB);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) cmac(nB[r], Vh[r * 4 + c], A[c]);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            sf[idx[r]] = make_float4(pp[r].x, pp[r].y, dp[r].x, dp[r].y);
-                            sb[idx[r]] = make_float4(nA[r].x, nA[r].y, nB[r].x, nB[r].y);
-                        }
-                    } else {
-                        float2 p[4], A[4], pp[4], nA[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) { p[c] = sf[idx[c]]; A[c] = sb[idx[c]]; }
-                        matvec4(Gi, p, pp);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
-                                cmac_conj(e1, A[i], pp[j]);
-                                red[2 * (i * 4 + j)] = e1.x;
-                                red[2 * (i * 4 + j) + 1] = e1.y;
-                            }
-                        matvec4(Gh, A, nA);
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) { sf[idx[r]] = pp[r]; sb[idx[r]] = nA[r]; }
+                    for (int c = 0; c < 4; ++c) {
+                        const float4 x = sf[idx[c]];
+                        const float4 y = sb[idx[c]];
+                        p[c] = lo2(x); d[c] = hi2(x); A[c] = lo2(y); B[c] = hi2(y);
                     }
-                }
-                warp_reduce_scatter<NV>(red, lane);
-                float* wr = wred + ((g & 1) * NW + warp) * 64;
+                    swaps<P2>(p, xs);
+                    matvec4<P2>(Gi, p, xs, pp);                       // psi^[k-1]
+                    swaps<P2>(pp, pps);
 #pragma unroll
-                for (int i = 0; i < NV / 32; ++i) wr[lane * (NV / 32) + i] = red[i];
-                __syncthreads();
-                if (tid < NV) {
-                    double sum = 0.0;
-                    for (int ww = 0; ww < NW; ++ww) sum += (double)wred[((g & 1) * NW + ww) * 64 + tid];
-                    acc[g * NV + tid] += sum;
+                    for (int r = 0; r < 4; ++r) {
+                        tt[r] = d[r];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Math<P2>::msub(tt[r], Vm[r * 4 + c], pp[c], pps[c]);
+                    }
+                    swaps<P2>(tt, xs);
+                    matvec4<P2>(Gi, tt, xs, dp);                      // dpsi^[k-1]
+                    swaps<P2>(dp, dps);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                            Math<P2>::cmac(e1, A[i], pp[j], pps[j]);
+                            red[2 * (i * 4 + j)] = e1.x;
+                            red[2 * (i * 4 + j) + 1] = e1.y;
+                            float2 e2 = make_float2(red[32 + 2 * (i * 4 + j)], red[32 + 2 * (i * 4 + j) + 1]);
+                            Math<P2>::cmac(e2, B[i], pp[j], pps[j]);
+                            Math<P2>::cmac(e2, A[i], dp[j], dps[j]);
+                            red[32 + 2 * (i * 4 + j)] = e2.x;
+                            red[32 + 2 * (i * 4 + j) + 1] = e2.y;
+                        }
+                    swaps<P2>(A, xs);
+                    matvec4<P2>(Gh, A, xs, nA);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        nB[r] = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Math<P2>::mac(nB[r], Vh[r * 4 + c], A[c], xs[c]);
+                    }
+                    swaps<P2>(B, xs);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) Math<P2>::mac(nB[r], Gh[r * 4 + c], B[c], xs[c]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        sf[idx[r]] = make_float4(pp[r].x, pp[r].y, dp[r].x, dp[r].y);
+                        sb[idx[r]] = make_float4(nA[r].x, nA[r].y, nB[r].x, nB[r].y);
+                    }
+                } else {
+                    float2 p[4], A[4], xs[4], pp[4], pps[4], nA[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) { p[c] = sf[idx[c]]; A[c] = sb[idx[c]]; }
+                    swaps<P2>(p, xs);
+                    matvec4<P2>(Gi, p, xs, pp);
+                    swaps<P2>(pp, pps);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                            Math<P2>::cmac(e1, A[i], pp[j], pps[j]);
+                            red[2 * (i * 4 + j)] = e1.x;
+                            red[2 * (i * 4 + j) + 1] = e1.y;
+                        }
+                    swaps<P2>(A, xs);
+                    matvec4<P2>(Gh, A, xs, nA);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) { sf[idx[r]] = pp[r]; sb[idx[r]] = nA[r]; }
                 }
+            }
+            warp_reduce_scatter<NV>(red, lane);
+            float* wr = wred + ((g & 1) * NW + warp) * 64;
+#pragma unroll
+            for (int i = 0; i < NV / 32; ++i) wr[lane * (NV / 32) + i] = red[i];
+            __syncthreads();
+            // Cross-warp sum of this gate in FP32, spread over NV threads; the
+            // double-buffered slot (gate parity) is rewritten two gates later.
+            if (tid < NV) {
+                float sum = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < NW; ++ww) sum += wred[((g & 1) * NW + ww) * 64 + tid];
+                acc[g * NV + tid] += sum;
             }
         }
 
-        // ------------------------------------------------- store co-states
-        if (mode & M_STORE_B) {
-            E* __restrict__ cout = reinterpret_cast<E*>(a.cout);
-            for (int m = tid; m < Lt; m += NT) {
-                const size_t addr = base + __ldg(&offlo[m & 63]) + __ldg(&offhi[m >> 6]);
-                const unsigned l = __ldg(&stlo[m & 63]) | __ldg(&sthi[m >> 6]);
-                cout[addr] = sb[swz(l)];
-            }
-        }
+        if (mode & M_STORE_B) store_tile<E, NT>(reinterpret_cast<E*>(a.cout), sb, tc, stlo, sthi, Lt);
         __syncthreads();
     }
 
     // One FP64 record per (gate, sample, CTA).
-    if (bwd) {
-        for (int i = tid; i < ngates * 64; i += NT) {
-            const int g = i >> 6, e = i & 63;
-            const int k = a.gates[goff + g].k;
-            double* dst = a.partial + (((size_t)k * a.n_samples + s) * a.cx_count + blockIdx.x) * 64;
-            dst[e] = e < NV ? acc[g * NV + e] : 0.0;
-        }
+    for (int i = tid; i < ngates * 64; i += NT) {
+        const int g = i >> 6, e = i & 63;
+        const int k = a.gates[goff + g].k;
+        double* dst = a.partial + (((size_t)k * a.n_samples + s) * a.cx_count + blockIdx.x) * 64;
+        dst[e] = e < NV ? (double)acc[g * NV + e] : 0.0;
     }
 }
 
-size_t tiled_smem_bytes(bool tangent, bool bwd, int w, int threads, int max_gates) {
+size_t tiled_smem_bytes(bool tangent, int mode, int w, int threads, int max_gates, int variant) {
+    const bool bwd = (mode & M_BWD) != 0;
     const size_t elt = tangent ? 16 : 8;
-    size_t b = elt << w;                       // forward states
-    if (bwd) b += elt << w;                    // co-states
-    b += (size_t)max_gates * 80 * 8;           // matrices
-    b += 2 * (size_t)(threads / 32) * 64 * 4;  // cross-warp buffer
-    if (bwd) b += (size_t)max_gates * (tangent ? 64 : 32) * 8;  // FP64 sums
+    const size_t mb = variant == 2 ? 16 : 8;
+    size_t b = elt << w;                                       // forward states
+    if (bwd) {
+        b += elt << w;                                         // co-states
+        b += (size_t)max_gates * ((mode & M_FWD) ? 5 : 4) * 16 * mb;   // matrices
+        b += 2 * (size_t)(threads / 32) * 64 * 4;              // cross-warp buffer
+        b += (size_t)max_gates * (tangent ? 64 : 32) * 4;      // FP32 sums
+    } else {
+        b += (size_t)max_gates * kFwdMats * 16 * mb;
+    }
     return b;
 }
 
-template <bool TAN, int NT>
-static cudaError_t set_limit() {
-    return cudaFuncSetAttribute(tiled_pass_kernel<TAN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <bool TAN, bool P2, int NT>
+static cudaError_t set_limits_one() {
+    cudaError_t e = cudaFuncSetAttribute(tiled_fwd_kernel<TAN, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tiled_bwd_kernel<TAN, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 227 * 1024);
 }
 
 cudaError_t tiled_set_smem_limits() {
     cudaError_t e;
-    if ((e = set_limit<true, 128>()) != cudaSuccess) return e;
-    if ((e = set_limit<true, 256>()) != cudaSuccess) return e;
-    if ((e = set_limit<true, 512>()) != cudaSuccess) return e;
-    if ((e = set_limit<false, 128>()) != cudaSuccess) return e;
-    if ((e = set_limit<false, 256>()) != cudaSuccess) return e;
-    return set_limit<false, 512>();
+#define HVP_SET(T, P, N) if ((e = set_limits_one<T, P, N>()) != cudaSuccess) return e
+    HVP_SET(true, false, 256); HVP_SET(true, false, 512); HVP_SET(true, true, 256); HVP_SET(true, true, 512);
+    HVP_SET(false, false, 256); HVP_SET(false, false, 512); HVP_SET(false, true, 256); HVP_SET(false, true, 512);
+#undef HVP_SET
+    return cudaSuccess;
 }
 
-cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, int n_gates,
-                         cudaStream_t st) {
+cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, int n_gates, cudaStream_t st,
+                         int variant) {
     const bool bwd = (a.mode & M_BWD) != 0;
-    const size_t smem = tiled_smem_bytes(tangent, bwd, w, threads, n_gates);
+    const bool p2 = variant == 2;
+    const size_t smem = tiled_smem_bytes(tangent, a.mode, w, threads, n_gates, variant);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     dim3 grid(a.cx_count, a.n_samples);
-#define HVP_LAUNCH(T, N) tiled_pass_kernel<T, N><<<grid, N, smem, st>>>(a)
-    if (tangent) {
-        if (threads == 128) HVP_LAUNCH(true, 128);
-        else if (threads == 256) HVP_LAUNCH(true, 256);
-        else if (threads == 512) HVP_LAUNCH(true, 512);
-        else return cudaErrorInvalidValue;
-    } else {
-        if (threads == 128) HVP_LAUNCH(false, 128);
-        else if (threads == 256) HVP_LAUNCH(false, 256);
-        else if (threads == 512) HVP_LAUNCH(false, 512);
-        else return cudaErrorInvalidValue;
+#define HVP_L(K, T, P, N) K<T, P, N><<<grid, N, smem, st>>>(a)
+#define HVP_PICK(K)                                                                                  \
+    if (tangent) {                                                                                   \
+        if (p2) { if (threads == 512) HVP_L(K, true, true, 512); else HVP_L(K, true, true, 256); }    \
+        else { if (threads == 512) HVP_L(K, true, false, 512); else HVP_L(K, true, false, 256); }     \
+    } else {                                                                                         \
+        if (p2) { if (threads == 512) HVP_L(K, false, true, 512); else HVP_L(K, false, true, 256); }  \
+        else { if (threads == 512) HVP_L(K, false, false, 512); else HVP_L(K, false, false, 256); }   \
     }
-#undef HVP_LAUNCH
+    if (threads != 256 && threads != 512) return cudaErrorInvalidValue;
+    if (bwd) {
+        HVP_PICK(tiled_bwd_kernel)
+    } else {
+        HVP_PICK(tiled_fwd_kernel)
+    }
+#undef HVP_PICK
+#undef HVP_L
     return cudaGetLastError();
 }
 

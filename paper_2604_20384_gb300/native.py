@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hvp.h")
 
 HVP_OK, HVP_EINVAL, HVP_ENOMEM, HVP_ECUDA, HVP_ETIMEOUT, HVP_ENONFINITE = 0, -1, -2, -3, -4, -5
 HVP_C64, HVP_C128 = 0, 1
-HVP_RIEMANNIAN, HVP_PHI_GIVEN, HVP_UNFUSED, HVP_NO_GRAPH = 1, 2, 4, 8
+HVP_RIEMANNIAN, HVP_PHI_GIVEN, HVP_UNFUSED, HVP_NO_GRAPH, HVP_AUTOTUNE = 1, 2, 4, 8, 16
 KINDS = {0: "prep", 1: "pass_fwd", 2: "pass_turnaround", 3: "pass_bwd", 4: "gate_init", 5: "gate_fwd",
          6: "gate_load_phi", 7: "gate_bwd", 8: "post"}
 OUT = dict(T=1, Omega=2, grad_e=3, hvp_e=4, grad_r=5, hvp_r=6, loss=7, env=8)
@@ -35,7 +35,8 @@ class HVPError(RuntimeError):
 class HVPConfig(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_layers", ctypes.c_int), ("n_samples", ctypes.c_int),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("checkpoint_stride", ctypes.c_int),
-                ("window", ctypes.c_int), ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("window", ctypes.c_int), ("threads", ctypes.c_int), ("variant", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 _lib = None
@@ -138,16 +139,17 @@ class Context:
 
     def __init__(self, n: int, n_layers: int, psi1q, ref, *, precision: str = "c64",
                  riemannian: bool = False, phi_given: bool = False, unfused: bool = False,
-                 graphs: bool = True, checkpoint_stride: int = 0, window: int = 0, device: int = 0,
-                 stream: int | None = None):
+                 graphs: bool = True, checkpoint_stride: int = 0, window: int = 0, threads: int = 0,
+                 variant: int = 0, autotune: bool = False, device: int = 0, stream: int | None = None):
         self._lib = load()
         psi1q = np.asarray(psi1q)
         self.n, self.n_layers, self.n_samples = n, n_layers, int(psi1q.shape[0])
         self.K = self._lib.hvp_num_gates(n, n_layers)
         flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
-                 | (HVP_UNFUSED if unfused else 0) | (0 if graphs else HVP_NO_GRAPH))
+                 | (HVP_UNFUSED if unfused else 0) | (0 if graphs else HVP_NO_GRAPH)
+                 | (HVP_AUTOTUNE if autotune else 0))
         cfg = HVPConfig(n, n_layers, self.n_samples, HVP_C128 if precision == "c128" else HVP_C64, flags,
-                        checkpoint_stride, window, device, stream)
+                        checkpoint_stride, window, threads, variant, device, stream)
         self._psi = _f64(psi1q)
         self._ref = _f64(ref)
         h = ctypes.c_void_p()
@@ -212,10 +214,10 @@ class Context:
         return c.reshape(self.K, 4, 4)
 
     def plan_info(self) -> dict:
-        info = (ctypes.c_longlong * 8)()
+        info = (ctypes.c_longlong * 10)()
         self._check(self._lib.hvp_plan_info(self._h, info))
         keys = ["K", "passes", "window", "checkpoint_stride", "launches_per_hvp", "device_mib",
-                "tiles_per_cta", "ctas_per_sample"]
+                "tiles_per_cta", "ctas_per_sample", "threads", "variant"]
         return dict(zip(keys, list(info)))
 
     def close(self):

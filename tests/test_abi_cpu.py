@@ -76,15 +76,15 @@ def test_init_validates_arguments_before_cuda():
     psi = np.zeros(4 * 6 * 2)
     ref = np.zeros(32 * 8)
     h = ctypes.c_void_p()
-    cfg = native.HVPConfig(1, 3, 2, 0, 0, 0, 0, 0, None)          # n < 2
+    cfg = native.HVPConfig(1, 3, 2, 0, 0, 0, 0, 0, 0, 0, None)          # n < 2
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
     assert not h.value
     assert b"n = 1" in lib.hvp_last_error(None)
-    cfg = native.HVPConfig(6, 3, 2, 7, 0, 0, 0, 0, None)          # bad precision
+    cfg = native.HVPConfig(6, 3, 2, 7, 0, 0, 0, 0, 0, 0, None)          # bad precision
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
-    cfg = native.HVPConfig(6, 3, 2, 0, 1 << 10, 0, 0, 0, None)    # unknown flag
+    cfg = native.HVPConfig(6, 3, 2, 0, 1 << 10, 0, 0, 0, 0, 0, None)    # unknown flag
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
-    cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 0, None)
+    cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 0, 0, 0, None)
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), None, native._ptr(ref)) == native.HVP_EINVAL
     bad = psi.copy()
     bad[3] = np.nan

@@ -71,6 +71,19 @@ def test_multi_pass_tiles_with_ragged_shapes(n, L, ns, window):
         _check(ctx, w, o, TOL["c64"])
 
 
+@pytest.mark.parametrize("threads,variant", [(256, 1), (256, 2), (512, 1), (512, 2)])
+def test_kernel_variants_match_oracle(threads, variant):
+    # every thread count and arithmetic form of the window-pass kernels
+    w = make_workload(15, 9, 6, seed=44)
+    o, phi = _oracle(w)
+    with native.Context(15, 9, w.psi1q, w.Uref, window=11, threads=threads, variant=variant) as ctx:
+        info = ctx.plan_info()
+        assert info["threads"] == threads and info["variant"] == variant and info["passes"] > 1
+        _check(ctx, w, o, TOL["c64"])
+        loss, grad = ctx.loss_grad(w.G)
+        assert rel(grad, o["grad"]) < TOL["c64"]
+
+
 def test_loss_and_gradient_only_call():
     w = make_workload(14, 6, 4, seed=3)
     o, phi = _oracle(w)
