@@ -98,6 +98,21 @@ int hvp_num_gates(int n, int n_layers);
 int hvp_init(hvp_ctx **out, const hvp_config *cfg, const double *psi_1q,
              const double *ref_data);
 
+/* Batch of independent circuits of uneven size evaluated together (one
+ * persistent kernel launch per call). cfgs[c], psi_1q[c] and ref_data[c]
+ * describe circuit c exactly as for hvp_init (complex64 path only; flags,
+ * device and stream are taken from cfgs[0]). The context then works with the
+ * same calls: G, V, grad and hvp concatenate the circuits' gates in order
+ * (sum_c K_c * 32 doubles), loss holds one double per circuit, HVP_OUT_T and
+ * HVP_OUT_OMEGA concatenate the circuits' samples; HVP_OUT_ENV and
+ * hvp_profile are not available. Circuits with n <= 12 pack 2^(12-n)
+ * samples into one shared-memory tile; larger ones run window passes with a
+ * per-sample chain of bounded device-side waits (HVP_ETIMEOUT if one
+ * expires). hvp_plan_info: info[1] = work items, info[6] = persistent CTAs,
+ * info[7] = circuits. */
+int hvp_init_batch(hvp_ctx **out, int n_circuits, const hvp_config *cfgs,
+                   const double *const *psi_1q, const double *const *ref_data);
+
 /* Loss and gradient (Alg. 1 without tangents, Alg. 2 first two steps).
  *   G    : host, K*32 doubles.
  *   loss : host, 1 double (may be NULL).

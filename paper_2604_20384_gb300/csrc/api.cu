@@ -82,6 +82,9 @@ struct hvp_ctx {
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_kind;
     std::vector<double> prof_flops, prof_bytes;
+    // batched contexts (hvp_init_batch)
+    BatchImpl* batch = nullptr;
+    int n_circuits = 0;
 
     size_t off_T() const { return 2; }
     size_t off_Om() const { return 2 + 2 * (size_t)cfg.n_samples; }
@@ -509,6 +512,13 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
 int call_impl(hvp_ctx* c, const double* G, const double* V, double* loss, double* grad, double* hvp_out) {
     if (!c) return HVP_EINVAL;
     if (!G) return fail(c, HVP_EINVAL, "G is NULL");
+    if (c->batch) {
+        const size_t n32b = 32 * (size_t)c->K;
+        if (!all_finite(G, n32b) || (V && !all_finite(V, n32b))) return fail(c, HVP_ENONFINITE, "G or V is not finite");
+        std::string e;
+        int rc = batch_call(c->batch, G, V, false, loss, grad, hvp_out, e);
+        return rc ? fail(c, rc, e) : HVP_OK;
+    }
     const size_t n32 = 32 * (size_t)c->K;
     const bool tan = V != nullptr;
     if (!all_finite(G, n32) || (tan && !all_finite(V, n32))) return fail(c, HVP_ENONFINITE, "G or V is not finite");
@@ -535,6 +545,14 @@ int call_impl(hvp_ctx* c, const double* G, const double* V, double* loss, double
 
 }  // namespace
 
+int hvp_internal_copy_phi(hvp_ctx* c, void* dst, size_t bytes) {
+    if (!c || c->unfused || c->dbl) return HVP_EINVAL;
+    if (cudaMemcpyAsync(dst, c->d_phi, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return HVP_ECUDA;
+    return HVP_OK;
+}
+
 extern "C" {
 
 int hvp_init(hvp_ctx** out, const hvp_config* cfg, const double* psi_1q, const double* ref_data) {
@@ -545,6 +563,53 @@ int hvp_init(hvp_ctx** out, const hvp_config* cfg, const double* psi_1q, const d
     int rc = init_impl(c, cfg, psi_1q, ref_data);
     if (rc) {
         g_init_error = c->err;
+        hvp_free(c);
+        return rc;
+    }
+    *out = c;
+    return HVP_OK;
+}
+
+int hvp_init_batch(hvp_ctx** out, int n_circuits, const hvp_config* cfgs, const double* const* psi_1q,
+                   const double* const* ref_data) {
+    if (!out) return fail(nullptr, HVP_EINVAL, "hvp_init_batch: out is NULL");
+    *out = nullptr;
+    if (n_circuits < 1 || !cfgs || !psi_1q || !ref_data)
+        return fail(nullptr, HVP_EINVAL, "hvp_init_batch: bad arguments");
+    for (int c = 0; c < n_circuits; ++c) {
+        const hvp_config& f = cfgs[c];
+        if (f.n < 2 || f.n > kMaxN || f.n_layers < 1 || f.n_samples < 1 || !psi_1q[c] || !ref_data[c])
+            return fail(nullptr, HVP_EINVAL, fmt("hvp_init_batch: circuit %d has a bad shape or NULL input", c));
+        if (f.precision != HVP_C64 || (f.flags & HVP_UNFUSED))
+            return fail(nullptr, HVP_EINVAL, "hvp_init_batch: batches run the complex64 window-pass path");
+        if (f.n > 12 && ((size_t)1 << f.n) * (size_t)f.n_samples > ((size_t)1 << 30))
+            return fail(nullptr, HVP_EINVAL, "hvp_init_batch: a circuit above 2^30 amplitudes");
+        if (!all_finite(psi_1q[c], (size_t)f.n_samples * f.n * 4)) return fail(nullptr, HVP_ENONFINITE, "psi_1q is not finite");
+    }
+    hvp_ctx* c = new (std::nothrow) hvp_ctx();
+    if (!c) return fail(nullptr, HVP_ENOMEM, "out of host memory");
+    c->cfg = cfgs[0];
+    c->n_circuits = n_circuits;
+    for (int i = 0; i < n_circuits; ++i) c->K += num_gates(cfgs[i].n, cfgs[i].n_layers);
+    if (cudaSetDevice(cfgs[0].device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, HVP_ECUDA, "hvp_init_batch: cudaSetDevice failed");
+    }
+    if (cfgs[0].stream) {
+        c->stream = (cudaStream_t)cfgs[0].stream;
+    } else if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        c->own_stream = true;
+    } else {
+        delete c;
+        return fail(nullptr, HVP_ECUDA, "hvp_init_batch: stream creation failed");
+    }
+    tiled_set_smem_limits();
+    std::string e;
+    int rc = batch_init(&c->batch, n_circuits, cfgs, psi_1q, ref_data, c->stream, e);
+    if (rc) {
+        c->batch = nullptr;
+        g_init_error = e;
         hvp_free(c);
         return rc;
     }
@@ -565,6 +630,11 @@ int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* lo
                 double* hvp_dev) {
     if (!c) return HVP_EINVAL;
     if (!G_dev) return fail(c, HVP_EINVAL, "G_dev is NULL");
+    if (c->batch) {
+        std::string e;
+        int rcb = batch_call(c->batch, G_dev, V_dev, true, loss_dev, grad_dev, hvp_dev, e);
+        return rcb ? fail(c, rcb, e) : HVP_OK;
+    }
     const size_t n32 = 32 * (size_t)c->K;
     const bool tan = V_dev != nullptr;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
@@ -585,6 +655,7 @@ int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* lo
 int hvp_profile(hvp_ctx* c, const double* G_dev, const double* V_dev, int max_launches, float* ms, int* kind,
                 double* flops, double* bytes) {
     if (!c || !G_dev || max_launches < 0) return HVP_EINVAL;
+    if (c->batch) return fail(c, HVP_EINVAL, "hvp_profile: not available for a batch context");
     const size_t n32 = 32 * (size_t)c->K;
     const bool tan = V_dev != nullptr;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
@@ -624,6 +695,11 @@ int hvp_profile(hvp_ctx* c, const double* G_dev, const double* V_dev, int max_la
 
 int hvp_get(hvp_ctx* c, int what, double* out) {
     if (!c || !out) return HVP_EINVAL;
+    if (c->batch) {
+        std::string e;
+        int rcb = batch_get(c->batch, what, out, e);
+        return rcb ? fail(c, rcb, e) : HVP_OK;
+    }
     size_t off = 0, len = 0;
     const size_t n32 = 32 * (size_t)c->K, ns = c->cfg.n_samples;
     switch (what) {
@@ -647,6 +723,10 @@ int hvp_get(hvp_ctx* c, int what, double* out) {
 
 int hvp_plan_info(const hvp_ctx* c, long long info[10]) {
     if (!c || !info) return HVP_EINVAL;
+    if (c->batch) {
+        batch_info(c->batch, info);
+        return HVP_OK;
+    }
     info[0] = c->K;
     info[1] = c->unfused ? c->K : c->P;
     info[2] = c->w;
@@ -662,6 +742,10 @@ int hvp_plan_info(const hvp_ctx* c, long long info[10]) {
 
 void hvp_free(hvp_ctx* c) {
     if (!c) return;
+    if (c->batch) {
+        batch_free(c->batch);
+        c->batch = nullptr;
+    }
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& g : c->gexec)
         if (g) cudaGraphExecDestroy(g);

@@ -42,7 +42,9 @@ int make_plan(int n, int L, int w, int b, Plan& plan);
 // Address and shared-memory index tables of one pass. "Address rank" m
 // enumerates the tile's 2^w amplitudes in increasing address order.
 struct DevPass {
-    int w;                  // local bits
+    int w;                  // local bits of a tile
+    int nq;                 // local bits that are qubits (w, or fewer when the
+                            // bits above nq select packed samples)
     int ng;                 // global bits (n - w)
     int n_gates;
     int gate_off;           // first entry in the DevGate array
@@ -143,4 +145,24 @@ cudaError_t launch_copy_out(const double* loss, const double2* grad, const doubl
 
 void set_thread_error(const char* msg);
 
+// Batched evaluation of many circuits (batch.cu).
+struct BatchImpl;
+
+
 }  // namespace hvp
+
+#include <string>
+#include "../../include/hvp.h"
+
+namespace hvp {
+int batch_init(BatchImpl** out, int n_circuits, const hvp_config* cfgs, const double* const* psi_1q,
+               const double* const* ref, cudaStream_t stream, std::string& err);
+int batch_call(BatchImpl* b, const double* G, const double* V, bool dev, double* loss, double* grad, double* hvp,
+               std::string& err);
+int batch_get(BatchImpl* b, int what, double* out, std::string& err);
+void batch_info(const BatchImpl* b, long long* info);
+void batch_free(BatchImpl* b);
+}  // namespace hvp
+
+// Copies a context's reference states (FP32, layout of its last pass) to dst.
+int hvp_internal_copy_phi(hvp_ctx* ctx, void* dst, size_t bytes);

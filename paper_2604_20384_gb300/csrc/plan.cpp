@@ -224,6 +224,7 @@ void build_dev_passes(const Plan& plan, std::vector<DevPass>& dps, std::vector<D
         DevPass d{};
         const int w = (int)pp.S.size();
         d.w = w;
+        d.nq = w;
         d.ng = n - w;
         d.n_gates = (int)pp.gates.size();
         d.gate_off = (int)dgs.size();

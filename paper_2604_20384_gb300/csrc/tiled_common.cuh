@@ -1,0 +1,325 @@
+// Device helpers of the window-pass kernels, shared by the per-pass kernels
+// (tiled.cu) and the persistent batch kernel (batch.cu). See tiled.cu for the
+// arithmetic of a pass.
+#pragma once
+
+#include "internal.h"
+
+namespace hvp {
+namespace tile {
+
+__device__ __forceinline__ unsigned insert0(unsigned x, int p) {
+    return ((x >> p) << (p + 1)) | (x & ((1u << p) - 1u));
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float2 swp(float2 x) { return make_float2(x.y, x.x); }
+
+// ---------------------------------------------------------------- arithmetic
+// Matrix element storage: scalar form keeps float2 {re, im}; packed form keeps
+// float4 {re, re, -im, im} so that acc += m x is
+//     acc = fma2({re, re}, {x.re, x.im}, acc); acc = fma2({-im, im}, {x.im, x.re}, acc).
+template <bool P2>
+struct Math;
+
+template <>
+struct Math<false> {
+    using M = float2;
+    static constexpr int kMatBytes = 8;
+    __device__ static __forceinline__ void mac(float2& acc, const M& m, float2 x, float2 /*xs*/) {
+        acc.x = fmaf(m.x, x.x, acc.x);
+        acc.x = fmaf(-m.y, x.y, acc.x);
+        acc.y = fmaf(m.x, x.y, acc.y);
+        acc.y = fmaf(m.y, x.x, acc.y);
+    }
+    __device__ static __forceinline__ void msub(float2& acc, const M& m, float2 x, float2 /*xs*/) {  // acc -= m x
+        acc.x = fmaf(-m.x, x.x, acc.x);
+        acc.x = fmaf(m.y, x.y, acc.x);
+        acc.y = fmaf(-m.x, x.y, acc.y);
+        acc.y = fmaf(-m.y, x.x, acc.y);
+    }
+    // acc += conj(a) x; (ar, ai) = a as given, x and its swap
+    __device__ static __forceinline__ void cmac(float2& acc, float2 a, float2 x, float2 /*xs*/) {
+        acc.x = fmaf(a.x, x.x, acc.x);
+        acc.x = fmaf(a.y, x.y, acc.x);
+        acc.y = fmaf(a.x, x.y, acc.y);
+        acc.y = fmaf(-a.y, x.x, acc.y);
+    }
+    __device__ static __forceinline__ M expand(float2 m) { return m; }
+};
+
+template <>
+struct Math<true> {
+    using M = float4;
+    static constexpr int kMatBytes = 16;
+    __device__ static __forceinline__ void mac(float2& acc, const M& m, float2 x, float2 xs) {
+        acc = __ffma2_rn(make_float2(m.x, m.y), x, acc);
+        acc = __ffma2_rn(make_float2(m.z, m.w), xs, acc);
+    }
+    __device__ static __forceinline__ void msub(float2& acc, const M& m, float2 x, float2 xs) {
+        acc = __ffma2_rn(make_float2(-m.x, -m.y), x, acc);
+        acc = __ffma2_rn(make_float2(-m.z, -m.w), xs, acc);
+    }
+    // acc += conj(a) x = {a.re, a.re} x + {a.im, -a.im} swap(x)
+    __device__ static __forceinline__ void cmac(float2& acc, float2 a, float2 x, float2 xs) {
+        acc = __ffma2_rn(make_float2(a.x, a.x), x, acc);
+        acc = __ffma2_rn(make_float2(a.y, -a.y), xs, acc);
+    }
+    __device__ static __forceinline__ M expand(float2 m) { return make_float4(m.x, m.x, -m.y, m.y); }
+};
+
+// y = M x for a 4x4 complex matrix in shared memory (row-major).
+template <bool P2>
+__device__ __forceinline__ void matvec4(const typename Math<P2>::M* __restrict__ M, const float2 (&x)[4],
+                                        const float2 (&xs)[4], float2 (&y)[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Math<P2>::mac(acc, M[r * 4 + c], x[c], xs[c]);
+        y[r] = acc;
+    }
+}
+
+template <bool P2>
+__device__ __forceinline__ void swaps(const float2 (&x)[4], float2 (&xs)[4]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) xs[c] = P2 ? swp(x[c]) : x[c];
+}
+
+// Reduce-scatter of NV values over a warp: afterwards lane l holds in v[0..NV/32)
+// the warp sums of components l*(NV/32) + i.
+template <int NV>
+__device__ __forceinline__ void warp_reduce_scatter(float (&v)[NV], int lane) {
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int off = 16 >> step;
+        const int half = (NV >> step) / 2;
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            float send = up ? v[i] : v[i + half];
+            float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+}
+
+template <bool TAN>
+struct Elt;
+template <>
+struct Elt<true> { using T = float4; };
+template <>
+struct Elt<false> { using T = float2; };
+
+__device__ __forceinline__ float2 lo2(float4 x) { return make_float2(x.x, x.y); }
+__device__ __forceinline__ float2 hi2(float4 x) { return make_float2(x.z, x.w); }
+
+// Matrix slots per gate in shared memory: forward kernel {G, V}; backward
+// kernel {G^-1, G^dag, V, V^dag} and, in the turnaround pass, also G.
+constexpr int kFwdMats = 2;
+
+// ------------------------------------------------------------ tile I/O
+struct TileCtx {
+    size_t base;
+    const uint32_t* offlo;
+    const uint32_t* offhi;
+};
+
+__device__ __forceinline__ size_t tile_base(const DevPass* __restrict__ P, unsigned t, size_t sample_off, int ng) {
+    size_t base = sample_off;
+    for (int r = 0; r < ng; ++r)
+        if ((t >> r) & 1u) base |= (size_t)1 << __ldg(&P->gpos[r]);
+    return base;
+}
+
+// CG: read through L2 only (data written by other CTAs of the same launch).
+template <typename E>
+__device__ __forceinline__ E ld_state(const E* p, bool cg) {
+    if (cg) return __ldcg(p);
+    return *p;
+}
+
+template <typename E, int NT, bool CG = false>
+__device__ __forceinline__ void load_tile(E* __restrict__ dst, const E* __restrict__ src, const TileCtx& tc,
+                                          const uint16_t* lo, const uint16_t* hi, int Lt) {
+    for (int m = threadIdx.x; m < Lt; m += NT) {
+        const size_t addr = tc.base + __ldg(&tc.offlo[m & 63]) + __ldg(&tc.offhi[m >> 6]);
+        const unsigned l = __ldg(&lo[m & 63]) | __ldg(&hi[m >> 6]);
+        dst[swz(l)] = ld_state(src + addr, CG);
+    }
+}
+
+template <typename E, int NT>
+__device__ __forceinline__ void store_tile(E* __restrict__ dst, const E* __restrict__ src, const TileCtx& tc,
+                                           const uint16_t* lo, const uint16_t* hi, int Lt) {
+    for (int m = threadIdx.x; m < Lt; m += NT) {
+        const size_t addr = tc.base + __ldg(&tc.offlo[m & 63]) + __ldg(&tc.offhi[m >> 6]);
+        const unsigned l = __ldg(&lo[m & 63]) | __ldg(&hi[m >> 6]);
+        dst[addr] = src[swz(l)];
+    }
+}
+
+// psi^[0] = (x)_q psi_{s,q}: tile factor of the fixed qubits times the factors
+// of the window qubits (Eq. costHS, product states). q1 points at the tile's
+// first sample; local index bits at and above nq select further samples
+// (several small samples packed into one tile), each n qubits apart.
+template <typename E, int NT>
+__device__ __forceinline__ void gen_tile(E* __restrict__ sf, const DevPass* __restrict__ P, const float2* q1,
+                                         unsigned t, int nq, int ng, int Lt, int n) {
+    float2 gamma = make_float2(1.f, 0.f);
+    for (int r = 0; r < ng; ++r) gamma = cmulf(gamma, __ldg(&q1[2 * __ldg(&P->gq[r]) + ((t >> r) & 1u)]));
+    for (int l = threadIdx.x; l < Lt; l += NT) {
+        const float2* qs = q1 + (size_t)(l >> nq) * 2 * n;
+        float2 amp = gamma;
+        for (int j = 0; j < nq; ++j) amp = cmulf(amp, __ldg(&qs[2 * __ldg(&P->sq[j]) + ((l >> j) & 1)]));
+        if constexpr (sizeof(E) == 16) sf[swz(l)] = E{amp.x, amp.y, 0.f, 0.f};
+        else sf[swz(l)] = amp;
+    }
+}
+
+// Stage matrices of the pass's gates into shared memory (expanded for the
+// packed form): nmat slots per gate, slot i holding Mats32 field which[i]
+// (fields: 0 G, 1 G^-1, 2 G^dag, 3 V, 4 V^dag).
+template <bool P2, int NT>
+__device__ __forceinline__ void stage_mats(typename Math<P2>::M* __restrict__ dst, const TiledArgs& a, int goff,
+                                           int ngates, int nmat, const int* which) {
+    for (int i = threadIdx.x; i < ngates * nmat * 16; i += NT) {
+        const int g = i / (nmat * 16), rem = i - g * nmat * 16, mi = rem >> 4, e = rem & 15;
+        const int k = __ldg(&a.gates[goff + g].k);
+        const float2 v = reinterpret_cast<const float2*>(a.mats + k)[which[mi] * 16 + e];
+        dst[i] = Math<P2>::expand(v);
+    }
+}
+
+// One forward gate over all groups of the tile.
+template <bool TAN, bool P2, int NT>
+__device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, const typename Math<P2>::M* Gm,
+                                         const typename Math<P2>::M* Vm, int u, int v, int Lt) {
+    const int plo = min(u, v), phi_ = max(u, v);
+    const unsigned mu = 1u << u, mv = 1u << v;
+    for (int q = threadIdx.x; q < (Lt >> 2); q += NT) {
+        const unsigned l0 = insert0(insert0(q, plo), phi_);
+        const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
+        if constexpr (TAN) {
+            float2 p[4], d[4], ps[4], ds[4], np[4], nd[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { const float4 x = sf[idx[c]]; p[c] = lo2(x); d[c] = hi2(x); }
+            swaps<P2>(p, ps);
+            swaps<P2>(d, ds);
+            matvec4<P2>(Gm, p, ps, np);
+            matvec4<P2>(Gm, d, ds, nd);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Math<P2>::mac(nd[r], Vm[r * 4 + c], p[c], ps[c]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sf[idx[r]] = make_float4(np[r].x, np[r].y, nd[r].x, nd[r].y);
+        } else {
+            float2 p[4], ps[4], np[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[c] = sf[idx[c]];
+            swaps<P2>(p, ps);
+            matvec4<P2>(Gm, p, ps, np);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sf[idx[r]] = np[r];
+        }
+    }
+}
+
+
+// One backward gate over all groups of the tile: recompute the forward states
+// before the gate, add the gate's environment sums to red[] (E then DE, real
+// and imaginary parts interleaved), update the co-states.
+template <bool TAN, bool P2, int NT, int NV>
+__device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, typename Elt<TAN>::T* __restrict__ sb,
+                                         const typename Math<P2>::M* Gi, const typename Math<P2>::M* Gh,
+                                         const typename Math<P2>::M* Vm, const typename Math<P2>::M* Vh, int u, int v,
+                                         int Lt, float (&red)[NV]) {
+    const int tid = threadIdx.x;
+    const int plo = min(u, v), phi_ = max(u, v);
+    const unsigned mu = 1u << u, mv = 1u << v;
+    for (int q = tid; q < (Lt >> 2); q += NT) {
+        const unsigned l0 = insert0(insert0(q, plo), phi_);
+        const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
+        if constexpr (TAN) {
+            float2 p[4], d[4], A[4], B[4], xs[4], pp[4], pps[4], tt[4], dp[4], dps[4], nA[4], nB[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float4 x = sf[idx[c]];
+                const float4 y = sb[idx[c]];
+                p[c] = lo2(x); d[c] = hi2(x); A[c] = lo2(y); B[c] = hi2(y);
+            }
+            swaps<P2>(p, xs);
+            matvec4<P2>(Gi, p, xs, pp);                       // psi^[k-1]
+            swaps<P2>(pp, pps);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                tt[r] = d[r];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Math<P2>::msub(tt[r], Vm[r * 4 + c], pp[c], pps[c]);
+            }
+            swaps<P2>(tt, xs);
+            matvec4<P2>(Gi, tt, xs, dp);                      // dpsi^[k-1]
+            swaps<P2>(dp, dps);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                    Math<P2>::cmac(e1, A[i], pp[j], pps[j]);
+                    red[2 * (i * 4 + j)] = e1.x;
+                    red[2 * (i * 4 + j) + 1] = e1.y;
+                    float2 e2 = make_float2(red[32 + 2 * (i * 4 + j)], red[32 + 2 * (i * 4 + j) + 1]);
+                    Math<P2>::cmac(e2, B[i], pp[j], pps[j]);
+                    Math<P2>::cmac(e2, A[i], dp[j], dps[j]);
+                    red[32 + 2 * (i * 4 + j)] = e2.x;
+                    red[32 + 2 * (i * 4 + j) + 1] = e2.y;
+                }
+            swaps<P2>(A, xs);
+            matvec4<P2>(Gh, A, xs, nA);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                nB[r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Math<P2>::mac(nB[r], Vh[r * 4 + c], A[c], xs[c]);
+            }
+            swaps<P2>(B, xs);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Math<P2>::mac(nB[r], Gh[r * 4 + c], B[c], xs[c]);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                sf[idx[r]] = make_float4(pp[r].x, pp[r].y, dp[r].x, dp[r].y);
+                sb[idx[r]] = make_float4(nA[r].x, nA[r].y, nB[r].x, nB[r].y);
+            }
+        } else {
+            float2 p[4], A[4], xs[4], pp[4], pps[4], nA[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { p[c] = sf[idx[c]]; A[c] = sb[idx[c]]; }
+            swaps<P2>(p, xs);
+            matvec4<P2>(Gi, p, xs, pp);
+            swaps<P2>(pp, pps);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                    Math<P2>::cmac(e1, A[i], pp[j], pps[j]);
+                    red[2 * (i * 4 + j)] = e1.x;
+                    red[2 * (i * 4 + j) + 1] = e1.y;
+                }
+            swaps<P2>(A, xs);
+            matvec4<P2>(Gh, A, xs, nA);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) { sf[idx[r]] = pp[r]; sb[idx[r]] = nA[r]; }
+        }
+    }
+}
+
+}  // namespace tile
+}  // namespace hvp

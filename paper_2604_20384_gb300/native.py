@@ -74,6 +74,9 @@ def load() -> ctypes.CDLL:
     lib.hvp_profile.restype = ctypes.c_int
     lib.hvp_hvp_noalloc.argtypes = [ctypes.c_int] * 3 + [vp] * 8
     lib.hvp_hvp_noalloc.restype = ctypes.c_int
+    lib.hvp_init_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(HVPConfig),
+                                   ctypes.POINTER(_dp), ctypes.POINTER(_dp)]
+    lib.hvp_init_batch.restype = ctypes.c_int
     lib.hvp_free.argtypes = [vp]
     lib.hvp_free.restype = None
     lib.hvp_last_error.argtypes = [vp]
@@ -236,3 +239,91 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchContext(Context):
+    """Many independent circuits evaluated together (hvp_init_batch).
+
+    circuits: list of (n, n_layers, psi1q, ref) tuples. Gates, directions and
+    derivatives are lists of per-circuit (K_c, 4, 4) arrays; the loss is one
+    value per circuit.
+    """
+
+    def __init__(self, circuits, *, riemannian: bool = False, phi_given: bool = False, graphs: bool = True,
+                 device: int = 0, stream: int | None = None):
+        self._lib = load()
+        nc = len(circuits)
+        flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
+                 | (0 if graphs else HVP_NO_GRAPH))
+        cfgs = (HVPConfig * nc)()
+        self._keep = []
+        psis = (_dp * nc)()
+        refs = (_dp * nc)()
+        self.Ks, self.ns = [], []
+        for c, (n, L, psi1q, ref) in enumerate(circuits):
+            psi1q = np.asarray(psi1q)
+            cfgs[c] = HVPConfig(n, L, int(psi1q.shape[0]), HVP_C64, flags, 0, 0, 0, 0, device, stream)
+            a, r = _f64(psi1q), _f64(ref)
+            self._keep += [a, r]
+            psis[c] = _ptr(a)
+            refs[c] = _ptr(r)
+            self.Ks.append(self._lib.hvp_num_gates(n, L))
+            self.ns.append(int(psi1q.shape[0]))
+        h = ctypes.c_void_p()
+        rc = self._lib.hvp_init_batch(ctypes.byref(h), nc, cfgs, psis, refs)
+        if rc != HVP_OK:
+            raise HVPError(rc, self._lib.hvp_last_error(None).decode())
+        self._h = h
+        self.riemannian = riemannian
+        self.K = sum(self.Ks)
+        self.n_samples = sum(self.ns)
+        self.n_circuits = nc
+
+    def _split(self, flat):
+        out, o = [], 0
+        for k in self.Ks:
+            out.append(flat[o:o + k])
+            o += k
+        return out
+
+    def loss_grad(self, Gs):
+        G = _f64(np.concatenate([np.asarray(g, dtype=np.complex128) for g in Gs]))
+        loss = np.zeros(self.n_circuits)
+        grad = np.zeros(32 * self.K)
+        self._check(self._lib.hvp_loss_grad(self._h, _ptr(G), _ptr(loss), _ptr(grad)))
+        return loss, self._split(grad.view(np.complex128).reshape(self.K, 4, 4))
+
+    def hvp(self, Gs, Vs):
+        G = _f64(np.concatenate([np.asarray(g, dtype=np.complex128) for g in Gs]))
+        V = _f64(np.concatenate([np.asarray(v, dtype=np.complex128) for v in Vs]))
+        loss = np.zeros(self.n_circuits)
+        grad = np.zeros(32 * self.K)
+        hv = np.zeros(32 * self.K)
+        self._check(self._lib.hvp_hvp(self._h, _ptr(G), _ptr(V), _ptr(loss), _ptr(grad), _ptr(hv)))
+        return (loss, self._split(grad.view(np.complex128).reshape(self.K, 4, 4)),
+                self._split(hv.view(np.complex128).reshape(self.K, 4, 4)))
+
+    def get(self, what: str):
+        if what == "loss":
+            out = np.zeros(self.n_circuits)
+            self._check(self._lib.hvp_get(self._h, OUT[what], _ptr(out)))
+            return out
+        if what in ("T", "Omega"):
+            out = np.zeros(2 * self.n_samples)
+            self._check(self._lib.hvp_get(self._h, OUT[what], _ptr(out)))
+            c = out.view(np.complex128)
+            res, o = [], 0
+            for ns in self.ns:
+                res.append(c[o:o + ns])
+                o += ns
+            return res
+        out = np.zeros(32 * self.K)
+        self._check(self._lib.hvp_get(self._h, OUT[what], _ptr(out)))
+        return self._split(out.view(np.complex128).reshape(self.K, 4, 4))
+
+    def plan_info(self) -> dict:
+        info = (ctypes.c_longlong * 10)()
+        self._check(self._lib.hvp_plan_info(self._h, info))
+        keys = ["K", "items", "tile_bits", "checkpoint_stride", "launches_per_hvp", "device_mib", "ctas",
+                "circuits", "threads", "variant"]
+        return dict(zip(keys, list(info)))

@@ -1,0 +1,61 @@
+"""Batched uneven circuits (one persistent launch per call) against the FP64
+oracle and against single-circuit contexts."""
+import numpy as np
+import pytest
+
+from common import rel
+from oracle import oracle
+from paper_2604_20384_gb300 import native
+from paper_2604_20384_gb300.inputs import make_workload, uneven_batch_shapes
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+SMALL = [(5, 4, 7), (9, 6, 19), (12, 5, 3), (13, 7, 5), (14, 9, 4), (8, 20, 33), (2, 1, 3), (16, 5, 2)]
+
+
+def _small_batch():
+    ws = [make_workload(n, L, ns, seed=100 + i) for i, (n, L, ns) in enumerate(SMALL)]
+    return ws, [(w.n, w.n_layers, w.psi1q, w.Uref) for w in ws]
+
+
+@pytest.mark.parametrize("riemannian,graphs", [(False, True), (True, False)])
+def test_small_uneven_batch_matches_oracle(riemannian, graphs):
+    ws, circuits = _small_batch()
+    with native.BatchContext(circuits, riemannian=riemannian, graphs=graphs) as b:
+        loss, grads, hvps = b.hvp([w.G for w in ws], [w.V for w in ws])
+        T, Om = b.get("T"), b.get("Omega")
+        l2, g2 = b.loss_grad([w.G for w in ws])
+    for i, w in enumerate(ws):
+        phi = oracle.reference_states(w.n, w.n_layers, w.Uref, w.psi1q)
+        o = oracle.evaluate(w.n, w.n_layers, w.G, w.V, w.psi1q, phi)
+        kg, kh = ("grad_r", "hvp_r") if riemannian else ("grad", "hvp")
+        assert abs((1 - loss[i]) - (1 - o["loss"])) <= TOL * (1 - o["loss"]) + 1e-13, i
+        assert rel(grads[i], o[kg]) < TOL, (i, rel(grads[i], o[kg]))
+        assert rel(hvps[i], o[kh]) < TOL, (i, rel(hvps[i], o[kh]))
+        assert rel(T[i], o["T"]) < TOL and rel(Om[i], o["Omega"]) < TOL
+        assert abs(l2[i] - loss[i]) < 1e-12
+        assert rel(g2[i], o[kg]) < TOL
+
+
+def test_full_uneven_batch_matches_single_contexts():
+    # 64 circuits, n ~ U{8..16}, L ~ U{4..20}, N_s log-uniform in [32, 512]
+    shapes = uneven_batch_shapes(64, seed=0)
+    ws = [make_workload(n, L, ns, s) for (n, L, ns, s) in shapes]
+    with native.BatchContext([(w.n, w.n_layers, w.psi1q, w.Uref) for w in ws]) as b:
+        info = b.plan_info()
+        assert info["circuits"] == 64
+        r1 = b.hvp([w.G for w in ws], [w.V for w in ws])
+        r2 = b.hvp([w.G for w in ws], [w.V for w in ws])
+    assert np.array_equal(r1[0], r2[0])
+    assert all(np.array_equal(a, c) for a, c in zip(r1[2], r2[2]))
+    assert np.all((r1[0] >= 0) & (r1[0] <= 1))
+    picks = sorted({int(i) for i in np.random.default_rng(3).choice(64, 6, replace=False)} |
+                   {int(np.argmax([w.n for w in ws])), int(np.argmin([w.n for w in ws]))})
+    for i in picks:
+        w = ws[i]
+        with native.Context(w.n, w.n_layers, w.psi1q, w.Uref) as c:
+            loss, g, h = c.hvp(w.G, w.V)
+        assert abs((1 - r1[0][i]) - (1 - loss)) <= TOL * (1 - loss) + 1e-13, i
+        assert rel(r1[1][i], g) < TOL, (i, w.n)
+        assert rel(r1[2][i], h) < TOL, (i, w.n)
