@@ -15,6 +15,7 @@ own GPU, and rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -29,6 +30,31 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(n=20, n_layers=16, n_samples=64, seed=0)
 METRIC = "HVPs/sec (loss+grad+HVP) at n=20,L=16,N_s=64; fraction of roofline"
 FP32_LANES_PER_SM, N_SM = 128, 152
+
+
+KERNEL_SOURCES = ["paper_2604_20384_gb300/csrc/tiled.cu", "paper_2604_20384_gb300/csrc/tiled_common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_n20_L16_Ns64.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per backward-kernel launch from the committed ncu capture, if
+    it was taken on the current kernel sources (else None)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            doc = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if doc.get("source_sha256") != kernel_source_hash():
+        return None
+    return doc.get("bwd_kernel_bytes_per_launch")
 
 
 def _peaks():
@@ -151,6 +177,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the unfused FP64 comparison sweep")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-circuit measurement")
     ap.add_argument("--samples", type=int, default=64,
                     help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
@@ -273,20 +300,32 @@ def main():
     # Dominant kernel: the window-pass kernel (forward, turnaround and backward
     # passes are one kernel); its arithmetic is FP32 SIMT, so the roofline is
     # the FP32 lane rate at the maximum SM clock.
-    pass_kinds = [k for k in by_kind if k.startswith("pass_")]
-    p_ms = sum(by_kind[k]["ms"] for k in pass_kinds)
-    p_fl = sum(by_kind[k]["flops"] for k in pass_kinds)
-    p_by = sum(by_kind[k]["bytes"] for k in pass_kinds)
-    p_n = sum(by_kind[k]["launches"] for k in pass_kinds)
+    # Dominant kernel: the backward window-pass kernel (backward passes and the
+    # turnaround pass). Its arithmetic is FP32 SIMT, so the roofline is the FP32
+    # lane rate at the maximum SM clock.
+    bwd_kinds = [k for k in ("pass_bwd", "pass_turnaround") if k in by_kind]
+    p_ms = sum(by_kind[k]["ms"] for k in bwd_kinds)
+    p_fl = sum(by_kind[k]["flops"] for k in bwd_kinds)
+    p_by = sum(by_kind[k]["bytes"] for k in bwd_kinds)
+    p_n = sum(by_kind[k]["launches"] for k in bwd_kinds)
     peaks, src = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s
-    achieved = p_fl / (p_ms / 1e3) / 1e12
+    achieved = (p_fl / p_n) / (p_ms / p_n / 1e3) / 1e12
+    fwd = by_kind.get("pass_fwd", {"ms": 0.0, "flops": 0.0, "launches": 0})
+    all_ms = sum(by_kind[k]["ms"] for k in by_kind if k.startswith("pass_"))
+    all_fl = sum(by_kind[k]["flops"] for k in by_kind if k.startswith("pass_"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "kernel": "tiled_pass_kernel<true,256> (all window passes)",
+                "frac": achieved / alu_peak, "traffic": recorded_traffic(),
+                "kernel": "tiled_bwd_kernel<tangent,scalar,256> (backward and turnaround window passes)",
                 "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
+                "algorithmic_bytes_per_launch": p_by / p_n,
                 "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
+                "forward_kernel": {"achieved": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9,
+                                   "frac": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9 / alu_peak,
+                                   "share_of_step": fwd["ms"] / total_ms},
+                "all_window_passes": {"achieved": all_fl / (all_ms / 1e3) / 1e12,
+                                      "frac": all_fl / (all_ms / 1e3) / 1e12 / alu_peak},
                 "hbm": {"achieved_gbs": p_by / (p_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
                         "frac": (p_by / (p_ms / 1e3) / 1e9) / peaks.get("hbm_gbs", 6800.0),
                         "peak_source": src}}
@@ -320,6 +359,37 @@ def main():
             f_ms = e0.elapsed_time(e1) / 2
         line["fp64_unfused"] = {"value": 1000.0 / f_ms, "unit": "HVPs/s", "ms_per_step": f_ms,
                                 "speedup_of_value": value / world / (1000.0 / f_ms)}
+
+    # ------------------------------- batched uneven circuits (secondary line)
+    if not args.no_batch and rank == 0:
+        from paper_2604_20384_gb300.inputs import uneven_batch_shapes
+
+        shapes = uneven_batch_shapes(64, seed=0)
+        bws = [make_workload(n, L, ns, sd) for (n, L, ns, sd) in shapes]
+        bstream = torch.cuda.Stream(device=dev)
+        with native.BatchContext([(x.n, x.n_layers, x.psi1q, x.Uref) for x in bws], device=local,
+                                 stream=bstream.cuda_stream) as bctx:
+            Gb = torch.from_numpy(np.concatenate([x.G for x in bws]).view(np.float64).reshape(-1).copy()).to(dev)
+            Vb = torch.from_numpy(np.concatenate([x.V for x in bws]).view(np.float64).reshape(-1).copy()).to(dev)
+            for _ in range(3):
+                bctx.hvp_dev(Gb.data_ptr(), Vb.data_ptr(), None, None, None)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(bstream)
+            nb = 10
+            for _ in range(nb):
+                bctx.hvp_dev(Gb.data_ptr(), Vb.data_ptr(), None, None, None)
+            e1.record(bstream)
+            torch.cuda.synchronize(dev)
+            b_ms = e0.elapsed_time(e1) / nb
+            binfo = bctx.plan_info()
+        amp_gates = sum((1 << x.n) * x.n_samples * x.K for x in bws)
+        line["batched_uneven"] = {
+            "workload": "64 circuits, n~U{8..16}, L~U{4..20}, N_s log-uniform 32..512 (seed 0)",
+            "value": 1000.0 / b_ms, "unit": "batch HVP evaluations/s", "ms_per_step": b_ms,
+            "circuit_hvps_per_s": 64 * 1000.0 / b_ms, "work_items": binfo["items"],
+            "persistent_ctas": binfo["ctas"], "launches_per_step": binfo["launches_per_hvp"],
+            "achieved_tflops": amp_gates * 384 / (b_ms / 1e3) / 1e12}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w).items() if k not in ("seconds_per_step", "steps")}

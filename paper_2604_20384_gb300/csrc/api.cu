@@ -12,6 +12,7 @@
 // others are recomputed segment by segment before the backward passes need
 // them.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -396,6 +397,46 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         c->own_stream = true;
     }
 
+    // Autotuning: time each (window, arithmetic) candidate with a temporary
+    // context and keep the fastest (identity gates: the cost of a sweep does
+    // not depend on the gate values).
+    hvp_config tuned = *cfg;
+    if ((cfg->flags & HVP_AUTOTUNE) && !c->unfused) {
+        std::vector<int> windows;
+        for (int wdw : {12, 11, 10})
+            if (wdw <= n || windows.empty()) windows.push_back(std::min(wdw, n));
+        std::sort(windows.begin(), windows.end());
+        windows.erase(std::unique(windows.begin(), windows.end()), windows.end());
+        std::vector<double> eye(32 * (size_t)c->K, 0.0), res_g(32 * (size_t)c->K), res_h(32 * (size_t)c->K);
+        for (int k = 0; k < c->K; ++k)
+            for (int d = 0; d < 4; ++d) eye[32 * (size_t)k + 2 * (d * 4 + d)] = 1.0;
+        double best = 1e300;
+        for (int wdw : windows)
+            for (int var : {1, 2}) {
+                hvp_config sc = *cfg;
+                sc.flags &= ~HVP_AUTOTUNE;
+                sc.window = wdw >= n ? 0 : wdw;
+                sc.threads = 256;
+                sc.variant = var;
+                hvp_ctx* tmp = nullptr;
+                if (hvp_init(&tmp, &sc, psi_1q, ref) != HVP_OK) continue;
+                double loss = 0.0;
+                int ok = hvp_hvp(tmp, eye.data(), eye.data(), &loss, res_g.data(), res_h.data());
+                auto t0 = std::chrono::steady_clock::now();
+                for (int r = 0; r < 2 && ok == HVP_OK; ++r)
+                    ok = hvp_hvp(tmp, eye.data(), eye.data(), &loss, res_g.data(), res_h.data());
+                const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                hvp_free(tmp);
+                if (ok == HVP_OK && dt < best) {
+                    best = dt;
+                    tuned.window = sc.window;
+                    tuned.threads = 256;
+                    tuned.variant = var;
+                }
+            }
+        cudaGetLastError();
+    }
+
     // Plan.
     int rc;
     if (c->unfused) {
@@ -405,9 +446,9 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         c->P = 0;
     } else {
         CUDA_TRY(c, tiled_set_smem_limits());
-        c->w = std::min(n, cfg->window ? cfg->window : 12);
-        c->threads = cfg->threads ? cfg->threads : 256;
-        c->variant = cfg->variant ? cfg->variant : 1;
+        c->w = std::min(n, tuned.window ? tuned.window : 12);
+        c->threads = tuned.threads ? tuned.threads : 256;
+        c->variant = tuned.variant ? tuned.variant : 1;
         if ((rc = make_plan(n, L, c->w, std::min(kLowBits, c->w - 1), c->plan))) return fail(c, rc, "planning failed");
         c->P = (int)c->plan.passes.size();
         for (auto& pp : c->plan.passes) c->max_gates = std::max(c->max_gates, (int)pp.gates.size());

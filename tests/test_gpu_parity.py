@@ -84,6 +84,15 @@ def test_kernel_variants_match_oracle(threads, variant):
         assert rel(grad, o["grad"]) < TOL["c64"]
 
 
+def test_autotuned_context_matches_oracle():
+    w = make_workload(14, 8, 6, seed=71)
+    o, phi = _oracle(w)
+    with native.Context(14, 8, w.psi1q, w.Uref, autotune=True) as ctx:
+        info = ctx.plan_info()
+        assert info["window"] in (10, 11, 12) and info["variant"] in (1, 2)
+        _check(ctx, w, o, TOL["c64"])
+
+
 def test_loss_and_gradient_only_call():
     w = make_workload(14, 6, 4, seed=3)
     o, phi = _oracle(w)
