@@ -78,7 +78,9 @@ typedef struct {
     int threads;           /* threads per CTA of the window-pass kernels,
                               256 or 512; 0 = auto                             */
     int variant;           /* arithmetic of the window-pass kernels: 1 scalar
-                              FP32 FMA, 2 packed fma.rn.f32x2; 0 = auto        */
+                              FP32 FMA, 2 packed fma.rn.f32x2, 3 scalar with
+                              two groups per thread iteration in the backward
+                              passes; 0 = auto                                 */
     int device;            /* CUDA device ordinal                              */
     void *stream;          /* cudaStream_t for all work; NULL = own stream     */
 } hvp_config;

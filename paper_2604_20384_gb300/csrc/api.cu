@@ -375,7 +375,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         return fail(c, HVP_EINVAL, "window must be 0 (auto) or in [6, 12]");
     if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
         return fail(c, HVP_EINVAL, "threads must be 0 (auto), 256 or 512");
-    if (cfg->variant < 0 || cfg->variant > 2) return fail(c, HVP_EINVAL, "variant must be 0 (auto), 1 or 2");
+    if (cfg->variant < 0 || cfg->variant > 3) return fail(c, HVP_EINVAL, "variant must be 0 (auto), 1, 2 or 3");
     if (((size_t)1 << n) * (size_t)ns > ((size_t)1 << 34))
         return fail(c, HVP_EINVAL, "2^n * n_samples above 2^34 amplitudes");
     if (!all_finite(psi_1q, (size_t)ns * n * 4)) return fail(c, HVP_ENONFINITE, "psi_1q is not finite");
@@ -412,7 +412,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
             for (int d = 0; d < 4; ++d) eye[32 * (size_t)k + 2 * (d * 4 + d)] = 1.0;
         double best = 1e300;
         for (int wdw : windows)
-            for (int var : {1, 2}) {
+            for (int var : {1, 2, 3}) {
                 hvp_config sc = *cfg;
                 sc.flags &= ~HVP_AUTOTUNE;
                 sc.window = wdw >= n ? 0 : wdw;

@@ -107,7 +107,7 @@ __device__ __forceinline__ void flush_records(const BatchArgs& A, const BCircuit
 template <bool TAN>
 __device__ __forceinline__ void stage_pass_mats(typename Math<false>::M* mats, const BatchArgs& A, const DevPass* P,
                                                 int nmat) {
-    const int which[5] = {1, 2, 3, 4, 0};   // G^-1, G^dag, V, V^dag, G
+    const int which[6] = {1, 2, 5, 4, 0, 3};   // G^-1, G^dag, Y, V^dag, G, V
     TiledArgs ta{};
     ta.gates = A.gates;
     ta.mats = A.mats;
@@ -119,7 +119,7 @@ __device__ __forceinline__ void fwd_gates(typename Elt<TAN>::T* sf, const typena
                                           const BatchArgs& A, const DevPass* P, int nmat, int Lt) {
     for (int g = 0; g < P->n_gates; ++g) {
         const DevGate dg = A.gates[P->gate_off + g];
-        fwd_gate<TAN, false, kBT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 2) * 16, dg.u, dg.v, Lt);
+        fwd_gate<TAN, false, kBT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 5) * 16, dg.u, dg.v, Lt);
         __syncthreads();
     }
 }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
     E* sf = reinterpret_cast<E*>(smem);
     E* sb = sf + Lt;
     MT* mats = reinterpret_cast<MT*>(sb + Lt);
-    float* wred = reinterpret_cast<float*>(mats + kMaxGatesPerPass * 5 * 16);
+    float* wred = reinterpret_cast<float*>(mats + kMaxGatesPerPass * 6 * 16);
     float* acc = wred + 2 * NW * 64;
     double* red64 = reinterpret_cast<double*>(acc + kMaxGatesPerPass * NV);
     float2* tw = reinterpret_cast<float2*>(red64 + NW * 4);   // 2 x kBMaxPack
@@ -211,9 +211,9 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 __syncthreads();
                 for (int p = 0; p < C.P; ++p) {
                     const DevPass* P = A.passes + C.pass_ofs + p;
-                    stage_pass_mats<TAN>(mats, A, P, 5);
+                    stage_pass_mats<TAN>(mats, A, P, 6);
                     __syncthreads();
-                    fwd_gates<TAN>(sf, mats, A, P, 5, Lt);
+                    fwd_gates<TAN>(sf, mats, A, P, 6, Lt);
                 }
                 // reference states into the co-state tile
                 for (int m = tid; m < Lt; m += kBT) {
@@ -262,10 +262,10 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 __syncthreads();
                 for (int p = C.P - 1; p >= 0; --p) {
                     const DevPass* P = A.passes + C.pass_ofs + p;
-                    stage_pass_mats<TAN>(mats, A, P, 5);
+                    stage_pass_mats<TAN>(mats, A, P, 6);
                     for (int i = tid; i < P->n_gates * NV; i += kBT) acc[i] = 0.f;
                     __syncthreads();
-                    bwd_gates<TAN>(sf, sb, mats, wred, acc, A, P, 5, Lt);
+                    bwd_gates<TAN>(sf, sb, mats, wred, acc, A, P, 6, Lt);
                     flush_records<NV>(A, C, P, acc, j);
                     __syncthreads();
                 }
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 const DevPass* P = A.passes + C.pass_ofs + p;
                 const E* xin = p == 0 ? nullptr : reinterpret_cast<const E*>(C.ckpt + (size_t)(p - 1) * C.ckpt_stride);
                 E* xout = reinterpret_cast<E*>(C.ckpt + (size_t)p * C.ckpt_stride);
-                stage_pass_mats<TAN>(mats, A, P, 5);
+                stage_pass_mats<TAN>(mats, A, P, 6);
                 __syncthreads();
                 double tot_acc[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int t = 0; t < C.tiles; ++t) {
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                     if (p == 0) gen_tile<E, kBT>(sf, P, C.psi1q + (size_t)s * C.n * 2, t, P->nq, P->ng, Lt, C.n);
                     else load_tile<E, kBT, true>(sf, xin, tc, P->in_lo, P->in_hi, Lt);
                     __syncthreads();
-                    fwd_gates<TAN>(sf, mats, A, P, 5, Lt);
+                    fwd_gates<TAN>(sf, mats, A, P, 6, Lt);
                     store_tile<E, kBT>(xout, sf, tc, P->out_lo, P->out_hi, Lt);
                     if (p == C.P - 1) {   // overlaps at the last cut
                         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -421,7 +421,7 @@ __global__ void bpost_loss_kernel(const BCircuit* __restrict__ circ, double* los
 size_t batch_smem(bool tan) {
     const size_t elt = tan ? 16 : 8;
     const int NV = tan ? 64 : 32;
-    return 2 * (elt << kBTile) + (size_t)kMaxGatesPerPass * 5 * 16 * 8 + 2 * (kBT / 32) * 64 * 4 +
+    return 2 * (elt << kBTile) + (size_t)kMaxGatesPerPass * 6 * 16 * 8 + 2 * (kBT / 32) * 64 * 4 +
            (size_t)kMaxGatesPerPass * NV * 4 + (kBT / 32) * 4 * 8 + 2 * kBMaxPack * 8;
 }
 

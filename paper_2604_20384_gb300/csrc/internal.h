@@ -83,8 +83,10 @@ enum PassMode : int {
     M_STORE_B = 32,   // store the co-states
 };
 
-struct Mats32 { float2 G[16], Ginv[16], Gh[16], V[16], Vh[16]; };
-struct Mats64 { double2 G[16], Ginv[16], Gh[16], V[16], Vh[16]; };
+// Per-gate matrices prepared in FP64 each call: G, G^-1, G^dag, V, V^dag and
+// Y = G^-1 V G^-1 (so that dpsi^[k-1] = G^-1 dpsi^[k] - Y psi^[k]).
+struct Mats32 { float2 G[16], Ginv[16], Gh[16], V[16], Vh[16], Y[16]; };
+struct Mats64 { double2 G[16], Ginv[16], Gh[16], V[16], Vh[16], Y[16]; };
 
 struct TiledArgs {
     const DevPass* pass;
@@ -103,7 +105,8 @@ struct TiledArgs {
 };
 
 // Launchers (return cudaError_t of the launch).
-// variant 1: scalar FP32 FMAs; 2: packed fma.rn.f32x2. threads: 256 or 512.
+// variant 1: scalar FP32 FMAs; 2: packed fma.rn.f32x2; 3: scalar, two groups
+// per iteration in the backward kernel. threads: 256 or 512.
 cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, int max_gates,
                          cudaStream_t st, int variant = 1);
 size_t tiled_smem_bytes(bool tangent, int mode, int w, int threads, int max_gates, int variant = 1);

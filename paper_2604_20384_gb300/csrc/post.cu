@@ -22,7 +22,8 @@ __device__ __forceinline__ bool dfinite(double2 a) { return isfinite(a.x) && isf
 // G^-1, G^dag, V^dag per gate; Gauss-Jordan elimination with partial pivoting
 // in FP64. A singular or non-finite gate sets status bit 1.
 template <typename MT, typename C>
-__device__ void store_mats(MT& m, const double2 (&G)[16], const double2 (&Gi)[16], const double2 (&V)[16]) {
+__device__ void store_mats(MT& m, const double2 (&G)[16], const double2 (&Gi)[16], const double2 (&V)[16],
+                           const double2 (&Y)[16]) {
     for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) {
             const int e = r * 4 + c;
@@ -32,7 +33,9 @@ __device__ void store_mats(MT& m, const double2 (&G)[16], const double2 (&Gi)[16
             gh.x = G[c * 4 + r].x; gh.y = -G[c * 4 + r].y;
             v.x = V[e].x; v.y = V[e].y;
             vh.x = V[c * 4 + r].x; vh.y = -V[c * 4 + r].y;
-            m.G[e] = g; m.Ginv[e] = gi; m.Gh[e] = gh; m.V[e] = v; m.Vh[e] = vh;
+            C y;
+            y.x = Y[e].x; y.y = Y[e].y;
+            m.G[e] = g; m.Ginv[e] = gi; m.Gh[e] = gh; m.V[e] = v; m.Vh[e] = vh; m.Y[e] = y;
         }
 }
 
@@ -76,8 +79,21 @@ __global__ void prep_kernel(const double2* __restrict__ Gin, const double2* __re
             ok = ok && dfinite(Gi[r * 4 + c]);
         }
     if (!ok) atomicOr(status, 1);
-    if (dbl) store_mats<Mats64, double2>(reinterpret_cast<Mats64*>(mats)[k], G, Gi, V);
-    else store_mats<Mats32, float2>(reinterpret_cast<Mats32*>(mats)[k], G, Gi, V);
+    double2 GV[16], Y[16];                       // Y = G^-1 V G^-1
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double2 a = make_double2(0.0, 0.0);
+            for (int t = 0; t < 4; ++t) a = dadd(a, dmul(Gi[r * 4 + t], V[t * 4 + c]));
+            GV[r * 4 + c] = a;
+        }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double2 a = make_double2(0.0, 0.0);
+            for (int t = 0; t < 4; ++t) a = dadd(a, dmul(GV[r * 4 + t], Gi[t * 4 + c]));
+            Y[r * 4 + c] = a;
+        }
+    if (dbl) store_mats<Mats64, double2>(reinterpret_cast<Mats64*>(mats)[k], G, Gi, V, Y);
+    else store_mats<Mats32, float2>(reinterpret_cast<Mats32*>(mats)[k], G, Gi, V, Y);
 }
 
 // env[s][k][e] = sum over CTAs of partial[k][s][cx][e]; one warp per (k, s).

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT, 2) tiled_fwd_kernel(TiledArgs a) {
 }
 
 // ----------------------------------------------------------- backward kernel
-template <bool TAN, bool P2, int NT>
+template <bool TAN, bool P2, int NT, bool G2 = false>
 __global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
     using MT = typename Math<P2>::M;
@@ -88,14 +88,14 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
     const int s = blockIdx.y;
     const int mode = a.mode;
 
-    const int nmat = (mode & M_FWD) ? 5 : 4;
+    const int nmat = (mode & M_FWD) ? 6 : 4;
     E* sf = reinterpret_cast<E*>(smem);
     E* sb = sf + Lt;
     MT* mats = reinterpret_cast<MT*>(sb + Lt);
     float* wred = reinterpret_cast<float*>(mats + ngates * nmat * 16);
     float* acc = wred + 2 * NW * 64;           // [ngates][NV] FP32 per CTA
 
-    const int which[5] = {1, 2, 3, 4, 0};      // G^-1, G^dag, V, V^dag, G
+    const int which[6] = {1, 2, 5, 4, 0, 3};   // G^-1, G^dag, Y, V^dag, G, V
     stage_mats<P2, NT>(mats, a, goff, ngates, nmat, which);
     for (int i = tid; i < ngates * NV; i += NT) acc[i] = 0.f;
 
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
         if (mode & M_FWD) {
             for (int g = 0; g < ngates; ++g) {
                 const DevGate dg = a.gates[goff + g];
-                fwd_gate<TAN, P2, NT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 2) * 16, dg.u, dg.v, Lt);
+                fwd_gate<TAN, P2, NT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 5) * 16, dg.u, dg.v, Lt);
                 __syncthreads();
             }
         }
@@ -142,7 +142,12 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
             float red[NV];
 #pragma unroll
             for (int e = 0; e < NV; ++e) red[e] = 0.f;
-            bwd_gate<TAN, P2, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
+            if constexpr (G2 && !P2) {
+                if (((Lt >> 2) % (2 * NT)) == 0) bwd_gate2<TAN, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
+                else bwd_gate<TAN, false, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
+            } else {
+                bwd_gate<TAN, P2, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
+            }
             warp_reduce_scatter<NV>(red, lane);
             float* wr = wred + ((g & 1) * NW + warp) * 64;
 #pragma unroll
@@ -174,11 +179,11 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
 size_t tiled_smem_bytes(bool tangent, int mode, int w, int threads, int max_gates, int variant) {
     const bool bwd = (mode & M_BWD) != 0;
     const size_t elt = tangent ? 16 : 8;
-    const size_t mb = variant == 2 ? 16 : 8;
+    const size_t mb = variant == 2 ? 16 : 8;   // packed form stores 16-byte matrix elements
     size_t b = elt << w;                                       // forward states
     if (bwd) {
         b += elt << w;                                         // co-states
-        b += (size_t)max_gates * ((mode & M_FWD) ? 5 : 4) * 16 * mb;   // matrices
+        b += (size_t)max_gates * ((mode & M_FWD) ? 6 : 4) * 16 * mb;   // matrices
         b += 2 * (size_t)(threads / 32) * 64 * 4;              // cross-warp buffer
         b += (size_t)max_gates * (tangent ? 64 : 32) * 4;      // FP32 sums
     } else {
@@ -192,7 +197,9 @@ static cudaError_t set_limits_one() {
     cudaError_t e = cudaFuncSetAttribute(tiled_fwd_kernel<TAN, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tiled_bwd_kernel<TAN, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(tiled_bwd_kernel<TAN, P2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess || P2) return e;
+    return cudaFuncSetAttribute(tiled_bwd_kernel<TAN, false, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 227 * 1024);
 }
 
@@ -222,7 +229,15 @@ cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, i
         else { if (threads == 512) HVP_L(K, false, false, 512); else HVP_L(K, false, false, 256); }   \
     }
     if (threads != 256 && threads != 512) return cudaErrorInvalidValue;
-    if (bwd) {
+    if (bwd && variant == 3) {
+        if (tangent) {
+            if (threads == 512) tiled_bwd_kernel<true, false, 512, true><<<grid, 512, smem, st>>>(a);
+            else tiled_bwd_kernel<true, false, 256, true><<<grid, 256, smem, st>>>(a);
+        } else {
+            if (threads == 512) tiled_bwd_kernel<false, false, 512, true><<<grid, 512, smem, st>>>(a);
+            else tiled_bwd_kernel<false, false, 256, true><<<grid, 256, smem, st>>>(a);
+        }
+    } else if (bwd) {
         HVP_PICK(tiled_bwd_kernel)
     } else {
         HVP_PICK(tiled_fwd_kernel)

@@ -232,8 +232,9 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
 
 
 // One backward gate over all groups of the tile: recompute the forward states
-// before the gate, add the gate's environment sums to red[] (E then DE, real
-// and imaginary parts interleaved), update the co-states.
+// before the gate (Vm holds Y = G^-1 V G^-1), add the gate's environment sums
+// to red[] (E then DE, real and imaginary parts interleaved), update the
+// co-states.
 template <bool TAN, bool P2, int NT, int NV>
 __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, typename Elt<TAN>::T* __restrict__ sb,
                                          const typename Math<P2>::M* Gi, const typename Math<P2>::M* Gh,
@@ -254,16 +255,14 @@ __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
                 p[c] = lo2(x); d[c] = hi2(x); A[c] = lo2(y); B[c] = hi2(y);
             }
             swaps<P2>(p, xs);
-            matvec4<P2>(Gi, p, xs, pp);                       // psi^[k-1]
+            swaps<P2>(d, tt);
+            matvec4<P2>(Gi, p, xs, pp);                       // psi^[k-1] = G^-1 psi^[k]
+            matvec4<P2>(Gi, d, tt, dp);                       // dpsi^[k-1] = G^-1 dpsi^[k] - Y psi^[k]
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) Math<P2>::msub(dp[r], Vm[r * 4 + c], p[c], xs[c]);
             swaps<P2>(pp, pps);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                tt[r] = d[r];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) Math<P2>::msub(tt[r], Vm[r * 4 + c], pp[c], pps[c]);
-            }
-            swaps<P2>(tt, xs);
-            matvec4<P2>(Gi, tt, xs, dp);                      // dpsi^[k-1]
             swaps<P2>(dp, dps);
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -317,6 +316,133 @@ __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
             matvec4<P2>(Gh, A, xs, nA);
 #pragma unroll
             for (int r = 0; r < 4; ++r) { sf[idx[r]] = pp[r]; sb[idx[r]] = nA[r]; }
+        }
+    }
+}
+
+// Two groups per iteration (scalar arithmetic): every matrix element read from
+// shared memory feeds both groups, and the two groups give independent
+// instruction streams. Requires (Lt / 4) % (2 NT) == 0.
+template <bool TAN, int NT, int NV>
+__device__ __forceinline__ void bwd_gate2(typename Elt<TAN>::T* __restrict__ sf, typename Elt<TAN>::T* __restrict__ sb,
+                                          const float2* Gi, const float2* Gh, const float2* Vm, const float2* Vh,
+                                          int u, int v, int Lt, float (&red)[NV]) {
+    using M = Math<false>;
+    const int tid = threadIdx.x;
+    const int plo = min(u, v), phi_ = max(u, v);
+    const unsigned mu = 1u << u, mv = 1u << v;
+    for (int q = tid; q < (Lt >> 2); q += 2 * NT) {
+        unsigned idx[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned l0 = insert0(insert0(q + h * NT, plo), phi_);
+            idx[h][0] = swz(l0); idx[h][1] = swz(l0 | mv); idx[h][2] = swz(l0 | mu); idx[h][3] = swz(l0 | mu | mv);
+        }
+        if constexpr (TAN) {
+            float2 p[2][4], d[2][4], A[2][4], B[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float4 x = sf[idx[h][c]];
+                    const float4 y = sb[idx[h][c]];
+                    p[h][c] = lo2(x); d[h][c] = hi2(x); A[h][c] = lo2(y); B[h][c] = hi2(y);
+                }
+            float2 pp[2][4], dp[2][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                pp[0][r] = pp[1][r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float2 m = Gi[r * 4 + c];
+                    M::mac(pp[0][r], m, p[0][c], p[0][c]);
+                    M::mac(pp[1][r], m, p[1][c], p[1][c]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {                     // dp = G^-1 d - Y p
+                dp[0][r] = dp[1][r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float2 m = Gi[r * 4 + c], y = Vm[r * 4 + c];
+                    M::mac(dp[0][r], m, d[0][c], d[0][c]);
+                    M::mac(dp[1][r], m, d[1][c], d[1][c]);
+                    M::msub(dp[0][r], y, p[0][c], p[0][c]);
+                    M::msub(dp[1][r], y, p[1][c], p[1][c]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                        M::cmac(e1, A[h][i], pp[h][j], pp[h][j]);
+                        red[2 * (i * 4 + j)] = e1.x;
+                        red[2 * (i * 4 + j) + 1] = e1.y;
+                        float2 e2 = make_float2(red[32 + 2 * (i * 4 + j)], red[32 + 2 * (i * 4 + j) + 1]);
+                        M::cmac(e2, B[h][i], pp[h][j], pp[h][j]);
+                        M::cmac(e2, A[h][i], dp[h][j], dp[h][j]);
+                        red[32 + 2 * (i * 4 + j)] = e2.x;
+                        red[32 + 2 * (i * 4 + j) + 1] = e2.y;
+                    }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) sf[idx[h][r]] = make_float4(pp[h][r].x, pp[h][r].y, dp[h][r].x, dp[h][r].y);
+            float2 nA[2][4], nB[2][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                nA[0][r] = nA[1][r] = nB[0][r] = nB[1][r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float2 g = Gh[r * 4 + c], vh = Vh[r * 4 + c];
+                    M::mac(nA[0][r], g, A[0][c], A[0][c]);
+                    M::mac(nA[1][r], g, A[1][c], A[1][c]);
+                    M::mac(nB[0][r], g, B[0][c], B[0][c]);
+                    M::mac(nB[1][r], g, B[1][c], B[1][c]);
+                    M::mac(nB[0][r], vh, A[0][c], A[0][c]);
+                    M::mac(nB[1][r], vh, A[1][c], A[1][c]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) sb[idx[h][r]] = make_float4(nA[h][r].x, nA[h][r].y, nB[h][r].x, nB[h][r].y);
+        } else {
+            float2 p[2][4], A[2][4], pp[2][4], nA[2][4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { p[h][c] = sf[idx[h][c]]; A[h][c] = sb[idx[h][c]]; }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                pp[0][r] = pp[1][r] = nA[0][r] = nA[1][r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float2 m = Gi[r * 4 + c], g = Gh[r * 4 + c];
+                    M::mac(pp[0][r], m, p[0][c], p[0][c]);
+                    M::mac(pp[1][r], m, p[1][c], p[1][c]);
+                    M::mac(nA[0][r], g, A[0][c], A[0][c]);
+                    M::mac(nA[1][r], g, A[1][c], A[1][c]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                        M::cmac(e1, A[h][i], pp[h][j], pp[h][j]);
+                        red[2 * (i * 4 + j)] = e1.x;
+                        red[2 * (i * 4 + j) + 1] = e1.y;
+                    }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) { sf[idx[h][r]] = pp[h][r]; sb[idx[h][r]] = nA[h][r]; }
         }
     }
 }

@@ -71,7 +71,7 @@ def test_multi_pass_tiles_with_ragged_shapes(n, L, ns, window):
         _check(ctx, w, o, TOL["c64"])
 
 
-@pytest.mark.parametrize("threads,variant", [(256, 1), (256, 2), (512, 1), (512, 2)])
+@pytest.mark.parametrize("threads,variant", [(256, 1), (256, 2), (512, 1), (512, 2), (256, 3), (512, 3)])
 def test_kernel_variants_match_oracle(threads, variant):
     # every thread count and arithmetic form of the window-pass kernels
     w = make_workload(15, 9, 6, seed=44)
