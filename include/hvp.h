@@ -63,6 +63,9 @@ extern "C" {
 #define HVP_NO_GRAPH 8    /* launch kernels directly instead of a CUDA graph   */
 #define HVP_AUTOTUNE 16   /* time the window/threads/arithmetic candidates at
                              hvp_init and keep the fastest (see hvp_plan_info) */
+#define HVP_FROBENIUS 32  /* loss, gradient and HVP of the sampled Frobenius
+                             cost C_F = 1 - (1/N_s) sum_s Re T_s (Eq. Frobenius,
+                             Eq. grad-costF, Eq. hvp-costF) instead of C      */
 
 typedef struct hvp_ctx hvp_ctx;
 

@@ -100,4 +100,8 @@ def evaluate(n: int, n_layers: int, G, V, psi1q, Uref) -> dict:
     grad = -(2.0 / ns) * np.einsum("s,skij->kij", T, E.conj())
     hvp = -(2.0 / ns) * (np.einsum("s,skij->kij", Omega, E.conj())
                          + np.einsum("s,skij->kij", T, DE.conj()))
-    return dict(loss=loss, T=T, Omega=Omega, E=E, DE=DE, grad=grad, hvp=hvp, phi=phis, psi=psis)
+    loss_f = 1.0 - np.mean(T.real)                       # Frobenius cost (Eq. Frobenius)
+    grad_f = -(1.0 / ns) * E.conj().sum(axis=0)
+    hvp_f = -(1.0 / ns) * DE.conj().sum(axis=0)
+    return dict(loss=loss, T=T, Omega=Omega, E=E, DE=DE, grad=grad, hvp=hvp, phi=phis, psi=psis,
+                loss_f=loss_f, grad_f=grad_f, hvp_f=hvp_f)

@@ -24,6 +24,9 @@
  *   - loss  C = 1 - (1/N_s) sum_s |T_s|^2                 (Eq. costHS)
  *   - gradient and HVP of C (Alg. 2 post-processing, Eq. grad-costHS,
  *     Eq. hvp-costHS), Riemannian forms (App. F, Eq. projec).
+ *   - the Frobenius cost C_F = 1 - (1/N_s) sum_s Re T_s (Eq. Frobenius), its
+ *     gradient -(1/N_s) sum_s conj(E_s) (Eq. grad-costF) and HVP
+ *     -(1/N_s) sum_s conj(DE_s) (Eq. hvp-costF), with Riemannian forms.
  *
  * Readings of the paper taken here:
  *   (1) Alg. 1 updates dphi before it is used in the HVP line; Eq. overlap-hvp
@@ -366,7 +369,8 @@ int oracle_hvp(int n, int n_layers, int n_samples,
                int ckpt_stride, int n_threads,
                double *loss, double *T_out, double *Omega_out, double *Omega_fwd_out,
                double *E_out, double *DE_out,
-               double *grad, double *hvp, double *grad_r, double *hvp_r, double *cuts_out)
+               double *grad, double *hvp, double *grad_r, double *hvp_r, double *cuts_out,
+               double *loss_f, double *grad_f, double *hvp_f, double *grad_fr, double *hvp_fr)
 {
     if (n < 2 || n > 30 || n_layers < 1 || n_samples < 1 || ckpt_stride < 1 || !G_in || !psi1q || !phi)
         return -1;
@@ -410,6 +414,9 @@ int oracle_hvp(int n, int n_layers, int n_samples,
     double fid = 0;
     for (int s = 0; s < n_samples; ++s) fid += creal(T[s] * conj(T[s]));
     if (loss) loss[0] = 1.0 - inv_n * fid;              /* Eq. costHS */
+    double reT = 0;
+    for (int s = 0; s < n_samples; ++s) reT += creal(T[s]);
+    if (loss_f) loss_f[0] = 1.0 - inv_n * reT;          /* Eq. Frobenius, sampled */
 
     for (int k = 0; k < K; ++k) {
         cplx g[16] = {0}, h[16] = {0};
@@ -430,6 +437,30 @@ int oracle_hvp(int n, int n_layers, int n_samples,
         }
         if (grad) store4(g, grad + 32 * (size_t)k);
         if (hvp) store4(h, hvp + 32 * (size_t)k);
+        /* Frobenius cost: grad L_F = -conj(dT/dG) (Eq. grad-costF),
+         * H L_F[V] = -conj(D(dT/dG)[V]) (Eq. hvp-costF), averaged over samples. */
+        cplx gf[16] = {0}, hf[16] = {0};
+        for (int s = 0; s < n_samples; ++s)
+            for (int e = 0; e < 16; ++e) {
+                gf[e] += -inv_n * conj(E[((size_t)s * K + k) * 16 + e]);
+                if (tan) hf[e] += -inv_n * conj(DE[((size_t)s * K + k) * 16 + e]);
+            }
+        if (grad_f) store4(gf, grad_f + 32 * (size_t)k);
+        if (hvp_f) store4(hf, hvp_f + 32 * (size_t)k);
+        if (grad_fr || hvp_fr) {
+            const cplx *Gk = G + 16 * k, *Vk = V + 16 * k;
+            cplx pr[16], gd[16], t1[16], t2[16], t3[16], t4[16], x[16];
+            project4(Gk, gf, pr);
+            if (grad_fr) store4(pr, grad_fr + 32 * (size_t)k);
+            if (hvp_fr) {
+                adjoint4(gf, gd);
+                matmul4(Vk, gd, t1); matmul4(t1, Gk, t2);
+                matmul4(Gk, gd, t3); matmul4(t3, Vk, t4);
+                for (int e = 0; e < 16; ++e) x[e] = hf[e] - 0.5 * t2[e] - 0.5 * t4[e];
+                project4(Gk, x, pr);
+                store4(pr, hvp_fr + 32 * (size_t)k);
+            }
+        }
         if (grad_r || hvp_r) {
             /* App. F: grad_R = P_G(grad);
              * H_R[V] = P_G(H[V] - V grad^dag G / 2 - G grad^dag V / 2). */

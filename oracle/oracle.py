@@ -27,7 +27,7 @@ def _load():
         lib.oracle_layout.restype = ctypes.c_int
         lib.oracle_reference_states.argtypes = [ctypes.c_int] * 3 + [_dp] * 3
         lib.oracle_reference_states.restype = ctypes.c_int
-        lib.oracle_hvp.argtypes = ([ctypes.c_int] * 3 + [_dp] * 4 + [ctypes.c_int] * 2 + [_dp] * 11)
+        lib.oracle_hvp.argtypes = ([ctypes.c_int] * 3 + [_dp] * 4 + [ctypes.c_int] * 2 + [_dp] * 16)
         lib.oracle_hvp.restype = ctypes.c_int
         lib.oracle_project.argtypes = [ctypes.c_int, _dp, _dp, _dp]
         lib.oracle_project.restype = ctypes.c_int
@@ -71,7 +71,8 @@ def evaluate(n: int, n_layers: int, G: np.ndarray, V: np.ndarray | None, psi1q: 
     """Loss, gradient, HVP (V given) and their Riemannian forms.
 
     Returns a dict with loss, T, Omega, Omega_fwd (N_s), grad, hvp, grad_r,
-    hvp_r (K,4,4) and optionally E, DE (N_s,K,4,4) and cuts (N_s,K+1).
+    hvp_r (K,4,4), the Frobenius-cost forms loss_f, grad_f, hvp_f, grad_fr,
+    hvp_fr, and optionally E, DE (N_s,K,4,4) and cuts (N_s,K+1).
     """
     lib = _load()
     G = _c128(G)
@@ -84,7 +85,9 @@ def evaluate(n: int, n_layers: int, G: np.ndarray, V: np.ndarray | None, psi1q: 
     out = dict(loss=np.zeros(1), T=np.zeros(ns, complex), Omega=np.zeros(ns, complex),
                Omega_fwd=np.zeros(ns, complex), grad=np.zeros((K, 4, 4), complex),
                hvp=np.zeros((K, 4, 4), complex), grad_r=np.zeros((K, 4, 4), complex),
-               hvp_r=np.zeros((K, 4, 4), complex))
+               hvp_r=np.zeros((K, 4, 4), complex), loss_f=np.zeros(1),
+               grad_f=np.zeros((K, 4, 4), complex), hvp_f=np.zeros((K, 4, 4), complex),
+               grad_fr=np.zeros((K, 4, 4), complex), hvp_fr=np.zeros((K, 4, 4), complex))
     E = np.zeros((ns, K, 4, 4), complex) if want_env else None
     DE = np.zeros((ns, K, 4, 4), complex) if want_env else None
     cuts = np.zeros((ns, K + 1), complex) if want_cuts else None
@@ -95,16 +98,18 @@ def evaluate(n: int, n_layers: int, G: np.ndarray, V: np.ndarray | None, psi1q: 
     rc = lib.oracle_hvp(n, n_layers, ns, f(G), f(Vc), f(psi1q), f(phi), ckpt_stride, threads,
                         _ptr(out["loss"]), f(out["T"]), f(out["Omega"]), f(out["Omega_fwd"]),
                         f(E), f(DE), f(out["grad"]), f(out["hvp"]), f(out["grad_r"]),
-                        f(out["hvp_r"]), f(cuts))
+                        f(out["hvp_r"]), f(cuts), _ptr(out["loss_f"]), f(out["grad_f"]), f(out["hvp_f"]),
+                        f(out["grad_fr"]), f(out["hvp_fr"]))
     if rc != 0:
         raise RuntimeError(f"oracle_hvp failed: {rc}")
     out["loss"] = float(out["loss"][0])
+    out["loss_f"] = float(out["loss_f"][0])
     if want_env:
         out["E"], out["DE"] = E, DE
     if want_cuts:
         out["cuts"] = cuts
     if V is None:
-        for key in ("hvp", "hvp_r", "Omega", "Omega_fwd"):
+        for key in ("hvp", "hvp_r", "Omega", "Omega_fwd", "hvp_f", "hvp_fr"):
             out.pop(key)
     return out
 

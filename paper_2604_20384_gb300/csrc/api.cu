@@ -288,6 +288,7 @@ int enqueue_all(hvp_ctx* c, bool tan) {
     p.n_samples = c->cfg.n_samples;
     p.cx_count = c->cx_count;
     p.tangent = tan ? 1 : 0;
+    p.frobenius = (c->cfg.flags & HVP_FROBENIUS) ? 1 : 0;
     CUDA_TRY(c, launch_post(p, c->stream));
     if ((rc = prof_mark(c, HVP_K_POST, 0.0, 0.0))) return rc;
     L += 4;
@@ -368,7 +369,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (L < 1) return fail(c, HVP_EINVAL, "n_layers must be >= 1");
     if (ns < 1) return fail(c, HVP_EINVAL, "n_samples must be >= 1");
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
-    if (cfg->flags & ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE))
+    if (cfg->flags & ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS))
         return fail(c, HVP_EINVAL, "unknown flag bits");
     if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
     if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))

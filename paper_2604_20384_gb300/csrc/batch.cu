@@ -67,6 +67,7 @@ struct BatchArgs {
     int* done;
     int* error;
     long long spin_limit;
+    int frob;           // Frobenius cost: co-state weights (1, 0) instead of (T_s, Omega_s)
 };
 
 // Block-wide sum of four FP32 values per thread into FP64 (red64 holds NW*4
@@ -240,8 +241,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                         const int s = j * C.sp + q;
                         C.T[s] = make_double2(tot[0], tot[1]);
                         C.Om[s] = make_double2(tot[2], tot[3]);
-                        tw[2 * q] = make_float2((float)tot[0], (float)tot[1]);
-                        tw[2 * q + 1] = make_float2((float)tot[2], (float)tot[3]);
+                        tw[2 * q] = A.frob ? make_float2(1.f, 0.f) : make_float2((float)tot[0], (float)tot[1]);
+                        tw[2 * q + 1] = A.frob ? make_float2(0.f, 0.f) : make_float2((float)tot[2], (float)tot[3]);
                     }
                 }
                 __syncthreads();
@@ -314,7 +315,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 const E* xin = reinterpret_cast<const E*>(C.ckpt + (size_t)p * C.ckpt_stride);
                 E* co = reinterpret_cast<E*>(C.co);
                 const double2 Ts = __ldcg(C.T + s), Os = __ldcg(C.Om + s);
-                const float2 Tq = make_float2((float)Ts.x, (float)Ts.y), Oq = make_float2((float)Os.x, (float)Os.y);
+                const float2 Tq = A.frob ? make_float2(1.f, 0.f) : make_float2((float)Ts.x, (float)Ts.y);
+                const float2 Oq = A.frob ? make_float2(0.f, 0.f) : make_float2((float)Os.x, (float)Os.y);
                 stage_pass_mats<TAN>(mats, A, P, 4);
                 for (int i = tid; i < P->n_gates * NV; i += kBT) acc[i] = 0.f;
                 __syncthreads();
@@ -359,7 +361,7 @@ __device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -
 __global__ void bpost_grad_kernel(const BCircuit* __restrict__ circ, const int* __restrict__ gate_circ,
                                   const double* __restrict__ records, const double2* __restrict__ G,
                                   const double2* __restrict__ V, double2* ge, double2* he, double2* gr, double2* hr,
-                                  int tangent) {
+                                  int tangent, int frob) {
     const int k = blockIdx.x, e = threadIdx.x;
     const BCircuit& C = circ[gate_circ[k]];
     const int kl = k - C.kofs;
@@ -372,7 +374,7 @@ __global__ void bpost_grad_kernel(const BCircuit* __restrict__ circ, const int* 
         RD.x += rec[(size_t)s * 64 + 32 + 2 * e];
         RD.y += rec[(size_t)s * 64 + 32 + 2 * e + 1];
     }
-    const double scale = -2.0 / C.ns_real;
+    const double scale = (frob ? -1.0 : -2.0) / C.ns_real;
     const double2 g = make_double2(scale * RE.x, -scale * RE.y);   // -(2/N) conj(sum conj(T) E)
     const double2 h = make_double2(scale * RD.x, -scale * RD.y);
     sG[e] = G[k * 16 + e];
@@ -404,11 +406,12 @@ __global__ void bpost_grad_kernel(const BCircuit* __restrict__ circ, const int* 
     }
 }
 
-__global__ void bpost_loss_kernel(const BCircuit* __restrict__ circ, double* loss) {
+__global__ void bpost_loss_kernel(const BCircuit* __restrict__ circ, double* loss, int frob) {
     const BCircuit& C = circ[blockIdx.x];
     __shared__ double sh[256];
     double a = 0.0;
-    for (int s = threadIdx.x; s < C.ns_real; s += blockDim.x) a += C.T[s].x * C.T[s].x + C.T[s].y * C.T[s].y;
+    for (int s = threadIdx.x; s < C.ns_real; s += blockDim.x)
+        a += frob ? C.T[s].x : C.T[s].x * C.T[s].x + C.T[s].y * C.T[s].y;
     sh[threadIdx.x] = a;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -534,6 +537,7 @@ int enqueue_batch(BatchImpl* b, bool tan, std::string& err) {
     A.error = b->d_sync + 1;
     A.done = b->d_sync + 2;
     A.spin_limit = 20000000;   // x 200 ns sleeps: a few seconds at most
+    A.frob = (b->flags & HVP_FROBENIUS) ? 1 : 0;
     const size_t smem = batch_smem(tan);
     if (tan) batch_kernel<true><<<b->grid, kBT, smem, st>>>(A);
     else batch_kernel<false><<<b->grid, kBT, smem, st>>>(A);
@@ -542,8 +546,9 @@ int enqueue_batch(BatchImpl* b, bool tan, std::string& err) {
                                               reinterpret_cast<double2*>(b->d_res + b->off_ge()),
                                               reinterpret_cast<double2*>(b->d_res + b->off_he()),
                                               reinterpret_cast<double2*>(b->d_res + b->off_gr()),
-                                              reinterpret_cast<double2*>(b->d_res + b->off_hr()), tan ? 1 : 0);
-    bpost_loss_kernel<<<b->nc, 256, 0, st>>>(b->d_circ, b->d_res);
+                                              reinterpret_cast<double2*>(b->d_res + b->off_hr()), tan ? 1 : 0,
+                                              A.frob);
+    bpost_loss_kernel<<<b->nc, 256, 0, st>>>(b->d_circ, b->d_res, A.frob);
     B_TRY(cudaGetLastError());
     b->launches = 4;
     return HVP_OK;

@@ -135,6 +135,7 @@ struct PostArgs {
     double2* grad_r;
     double2* hvp_r;
     int K, n_samples, cx_count, tangent;
+    int frobenius;          // 1: derivatives of C_F = 1 - mean Re T instead of C
 };
 cudaError_t launch_post(const PostArgs& p, cudaStream_t st);
 cudaError_t launch_prep(const double2* G, const double2* V, void* mats, bool dbl, int K, int* status,

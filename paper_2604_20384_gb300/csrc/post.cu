@@ -145,26 +145,30 @@ __global__ void overlaps_kernel(const double* __restrict__ env, const double2* _
 __global__ void grad_kernel(const double* __restrict__ env, const double2* __restrict__ G,
                             const double2* __restrict__ V, const double2* __restrict__ T,
                             const double2* __restrict__ Om, double2* ge, double2* he, double2* gr, double2* hr,
-                            int K, int ns, int tangent) {
+                            int K, int ns, int tangent, int frob) {
     const int k = blockIdx.x, e = threadIdx.x;
-    __shared__ double2 sG[16], sV[16], sg[16], sh[16], sX[16];
-    const double scale = -2.0 / ns;
+    __shared__ double2 sG[16], sV[16], sg[16], sX[16];
     double2 g = make_double2(0.0, 0.0), h = make_double2(0.0, 0.0);
     for (int s = 0; s < ns; ++s) {
         const double2* Es = reinterpret_cast<const double2*>(env + ((size_t)s * K + k) * 64);
         const double2 E = dconj(Es[e]);
-        g = dadd(g, dmul(T[s], E));                    // T_s conj(E_s)
-        if (tangent) {
-            h = dadd(h, dmul(Om[s], E));               // Omega_s conj(E_s)
-            h = dadd(h, dmul(T[s], dconj(Es[16 + e])));  // T_s conj(DE_s)
+        if (frob) {                                     // C_F: -(1/N) sum conj(E_s), conj(DE_s)
+            g = dadd(g, E);
+            if (tangent) h = dadd(h, dconj(Es[16 + e]));
+        } else {
+            g = dadd(g, dmul(T[s], E));                 // T_s conj(E_s)
+            if (tangent) {
+                h = dadd(h, dmul(Om[s], E));            // Omega_s conj(E_s)
+                h = dadd(h, dmul(T[s], dconj(Es[16 + e])));  // T_s conj(DE_s)
+            }
         }
     }
+    const double scale = (frob ? -1.0 : -2.0) / ns;
     g = dscale(g, scale);
     h = dscale(h, scale);
     sG[e] = G[k * 16 + e];
     sV[e] = tangent ? V[k * 16 + e] : make_double2(0.0, 0.0);
     sg[e] = g;
-    sh[e] = h;
     ge[k * 16 + e] = g;
     if (tangent) he[k * 16 + e] = h;
     __syncthreads();
@@ -187,17 +191,17 @@ __global__ void grad_kernel(const double* __restrict__ env, const double2* __res
     }
 }
 
-__global__ void loss_kernel(const double2* __restrict__ T, double* loss, int ns) {
+__global__ void loss_kernel(const double2* __restrict__ T, double* loss, int ns, int frob) {
     __shared__ double sh[256];
     double a = 0.0;
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) a += T[s].x * T[s].x + T[s].y * T[s].y;
+    for (int s = threadIdx.x; s < ns; s += blockDim.x) a += frob ? T[s].x : T[s].x * T[s].x + T[s].y * T[s].y;
     sh[threadIdx.x] = a;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) loss[0] = 1.0 - sh[0] / ns;   // Eq. costHS
+    if (threadIdx.x == 0) loss[0] = 1.0 - sh[0] / ns;   // Eq. costHS (Eq. Frobenius with frob)
 }
 
 __global__ void psi1q_convert_kernel(const double* __restrict__ in, float2* out, size_t count) {
@@ -232,8 +236,8 @@ cudaError_t launch_post(const PostArgs& p, cudaStream_t st) {
     reduce_kernel<<<(pairs + 7) / 8, 256, 0, st>>>(p.partial, p.env, p.K, p.n_samples, p.cx_count);
     overlaps_kernel<<<p.n_samples, 256, 0, st>>>(p.env, p.G, p.V, p.T, p.Omega, p.K, p.tangent);
     grad_kernel<<<p.K, 16, 0, st>>>(p.env, p.G, p.V, p.T, p.Omega, p.grad_e, p.hvp_e, p.grad_r, p.hvp_r, p.K,
-                                     p.n_samples, p.tangent);
-    loss_kernel<<<1, 256, 0, st>>>(p.T, p.loss, p.n_samples);
+                                     p.n_samples, p.tangent, p.frobenius);
+    loss_kernel<<<1, 256, 0, st>>>(p.T, p.loss, p.n_samples, p.frobenius);
     return cudaGetLastError();
 }
 

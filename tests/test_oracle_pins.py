@@ -317,3 +317,113 @@ def test_riemannian_hessian_self_adjoint():
 def test_near_solution_workload_has_order_one_overlaps():
     w, phi, o = oracle_case(6, 3, 8, seed=0, near_solution=0.1)
     assert np.min(np.abs(o["T"])) > 0.5
+
+
+# ---------------------------------------------------------------- Frobenius cost (Eq. Frobenius)
+
+def test_frobenius_cost_against_dense_and_differences():
+    w, phi, o = oracle_case(5, 4, 6, seed=41)
+    d = dense.evaluate(5, 4, w.G, w.V, w.psi1q, w.Uref)
+    assert abs(o["loss_f"] - d["loss_f"]) < 1e-13
+    assert rel(o["grad_f"], d["grad_f"]) < 1e-12 and rel(o["hvp_f"], d["hvp_f"]) < 1e-12
+
+    def lf(G):
+        return oracle.evaluate(5, 4, G, None, w.psi1q, phi)["loss_f"]
+
+    h = 1e-5
+    for (k, i, j) in [(0, 0, 0), (3, 2, 1), (w.K - 1, 3, 3)]:
+        e = np.zeros_like(w.G)
+        e[k, i, j] = h
+        dx = (lf(w.G + e) - lf(w.G - e)) / (2 * h)
+        dy = (lf(w.G + 1j * e) - lf(w.G - 1j * e)) / (2 * h)
+        assert abs(o["grad_f"][k, i, j] - (dx + 1j * dy)) < 1e-9
+
+    def gf(G):
+        return oracle.evaluate(5, 4, G, None, w.psi1q, phi)["grad_f"]
+
+    hh = 1e-3
+    fd = (4 * (gf(w.G + hh / 2 * w.V) - gf(w.G - hh / 2 * w.V)) / hh - (gf(w.G + hh * w.V) - gf(w.G - hh * w.V)) / (2 * hh)) / 3
+    assert rel(o["hvp_f"], fd) < 1e-8
+
+
+def test_frobenius_solution_point():
+    # G = U_ref: T_s = 1 so C_F = 0 and its Riemannian gradient vanishes.
+    w = make_workload(6, 3, 5, seed=43)
+    phi = oracle.reference_states(6, 3, w.Uref, w.psi1q)
+    o = oracle.evaluate(6, 3, w.Uref, w.V, w.psi1q, phi)
+    assert abs(o["loss_f"]) < 1e-13
+    assert np.max(np.abs(o["grad_fr"])) < 1e-13
+
+
+# ---------------------------------------------------------------- translation invariance (App. E)
+
+def test_translation_invariant_chain_rule():
+    # Layer-gate derivatives are the per-gate sums over the layer (App. E):
+    # checked against central differences in the layer gates themselves.
+    from paper_2604_20384_gb300.translation import contract, expand
+
+    n, L, ns = 6, 4, 5
+    w = make_workload(n, L, ns, seed=51)
+    Gl = np.stack([w.G[0], w.G[3], w.G[5], w.G[8]])      # one gate of each layer
+    Vl = np.stack([w.V[0], w.V[3], w.V[5], w.V[8]])
+    phi = oracle.reference_states(n, L, w.Uref, w.psi1q)
+    o = oracle.evaluate(n, L, expand(Gl, n, L), expand(Vl, n, L), w.psi1q, phi)
+    g_l, h_l = contract(o["grad"], n, L), contract(o["hvp"], n, L)
+
+    def loss_l(G):
+        return oracle.evaluate(n, L, expand(G, n, L), None, w.psi1q, phi)["loss"]
+
+    def grad_l(G):
+        return contract(oracle.evaluate(n, L, expand(G, n, L), None, w.psi1q, phi)["grad"], n, L)
+
+    h = 1e-5
+    for (l, i, j) in [(0, 0, 1), (2, 3, 3), (3, 1, 2)]:
+        e = np.zeros_like(Gl)
+        e[l, i, j] = h
+        dx = (loss_l(Gl + e) - loss_l(Gl - e)) / (2 * h)
+        dy = (loss_l(Gl + 1j * e) - loss_l(Gl - 1j * e)) / (2 * h)
+        assert abs(g_l[l, i, j] - (dx + 1j * dy)) < 1e-9
+    hh = 1e-3
+    fd = (4 * (grad_l(Gl + hh / 2 * Vl) - grad_l(Gl - hh / 2 * Vl)) / hh
+          - (grad_l(Gl + hh * Vl) - grad_l(Gl - hh * Vl)) / (2 * hh)) / 3
+    assert rel(h_l, fd) < 1e-8
+
+
+# ---------------------------------------------------------------- dense Riemannian Hessian (App. G)
+
+def test_pauli_tangent_basis_is_orthonormal_tangent():
+    from paper_2604_20384_gb300.spectrum import tangent_basis
+
+    w = make_workload(4, 2, 1, seed=3)
+    B = tangent_basis(w.G)
+    Bf = B.reshape(B.shape[0], -1)
+    gram = np.real(Bf.conj() @ Bf.T)
+    assert np.max(np.abs(gram - np.eye(B.shape[0]))) < 1e-13
+    P = np.stack([oracle.project(w.G, B[j]) for j in range(B.shape[0])])   # already tangent
+    assert np.max(np.abs(P - B)) < 1e-13
+
+
+def test_riemannian_hessian_from_oracle_hvps():
+    from paper_2604_20384_gb300.spectrum import riemannian_hessian, spectrum
+
+    n, L, ns = 4, 3, 4
+    w = make_workload(n, L, ns, seed=91)
+    phi = oracle.reference_states(n, L, w.Uref, w.psi1q)
+    H = riemannian_hessian(lambda G, V: oracle.evaluate(n, L, G, V, w.psi1q, phi)["hvp_r"], w.G)
+    assert np.max(np.abs(H - H.T)) < 1e-12 * np.max(np.abs(H))
+    # the quadratic form along a basis vector equals the second derivative along
+    # its geodesic (App. F); check one diagonal entry
+    from paper_2604_20384_gb300.spectrum import tangent_basis
+    E = tangent_basis(w.G)[5]
+    X = np.stack([w.G[k].conj().T @ E[k] for k in range(w.K)])
+    h = 1e-3
+
+    def c(t):
+        return oracle.evaluate(n, L, np.stack([w.G[k] @ expm_skew(t * X[k]) for k in range(w.K)]), None,
+                               w.psi1q, phi)["loss"]
+
+    d2 = (-c(2 * h) + 16 * c(h) - 30 * c(0) + 16 * c(-h) - c(-2 * h)) / (12 * h * h)
+    assert abs(H[5, 5] - d2) < 1e-6 * max(1.0, abs(d2))
+    # at the solution G = U_ref the Riemannian Hessian is positive semidefinite
+    H0 = riemannian_hessian(lambda G, V: oracle.evaluate(n, L, G, V, w.psi1q, phi)["hvp_r"], w.Uref)
+    assert spectrum(H0)[0] > -1e-10
