@@ -297,9 +297,6 @@ def main():
                                         flops=float(prof["flops"][sel].sum()),
                                         bytes=float(prof["bytes"][sel].sum()))
     total_ms = float(prof["ms"].sum())
-    # Dominant kernel: the window-pass kernel (forward, turnaround and backward
-    # passes are one kernel); its arithmetic is FP32 SIMT, so the roofline is
-    # the FP32 lane rate at the maximum SM clock.
     # Dominant kernel: the backward window-pass kernel (backward passes and the
     # turnaround pass). Its arithmetic is FP32 SIMT, so the roofline is the FP32
     # lane rate at the maximum SM clock.

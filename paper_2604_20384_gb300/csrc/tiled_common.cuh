@@ -72,9 +72,8 @@ struct Math<true> {
 };
 
 // y = M x for a 4x4 complex matrix in shared memory (row-major).
-template <bool P2>
-__device__ __forceinline__ void matvec4(const typename Math<P2>::M* __restrict__ M, const float2 (&x)[4],
-                                        const float2 (&xs)[4], float2 (&y)[4]) {
+template <bool P2, class MA>
+__device__ __forceinline__ void matvec4(MA M, const float2 (&x)[4], const float2 (&xs)[4], float2 (&y)[4]) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         float2 acc = make_float2(0.f, 0.f);
@@ -196,9 +195,11 @@ __device__ __forceinline__ void stage_mats(typename Math<P2>::M* __restrict__ ds
 }
 
 // One forward gate over all groups of the tile.
-template <bool TAN, bool P2, int NT>
-__device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, const typename Math<P2>::M* Gm,
-                                         const typename Math<P2>::M* Vm, int u, int v, int Lt) {
+// MA: matrix accessor, a pointer into shared memory or an object whose
+// operator[] reads another state space (e.g. constant memory).
+template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*>
+__device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, MA Gm, MA Vm, int u, int v,
+                                         int Lt) {
     const int plo = min(u, v), phi_ = max(u, v);
     const unsigned mu = 1u << u, mv = 1u << v;
     for (int q = threadIdx.x; q < (Lt >> 2); q += NT) {
@@ -235,11 +236,9 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
 // before the gate (Vm holds Y = G^-1 V G^-1), add the gate's environment sums
 // to red[] (E then DE, real and imaginary parts interleaved), update the
 // co-states.
-template <bool TAN, bool P2, int NT, int NV>
+template <bool TAN, bool P2, int NT, int NV, class MA = const typename Math<P2>::M*>
 __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, typename Elt<TAN>::T* __restrict__ sb,
-                                         const typename Math<P2>::M* Gi, const typename Math<P2>::M* Gh,
-                                         const typename Math<P2>::M* Vm, const typename Math<P2>::M* Vh, int u, int v,
-                                         int Lt, float (&red)[NV]) {
+                                         MA Gi, MA Gh, MA Vm, MA Vh, int u, int v, int Lt, float (&red)[NV]) {
     const int tid = threadIdx.x;
     const int plo = min(u, v), phi_ = max(u, v);
     const unsigned mu = 1u << u, mv = 1u << v;
