@@ -111,9 +111,12 @@ int hvp_init(hvp_ctx **out, const hvp_config *cfg, const double *psi_1q,
  * (sum_c K_c * 32 doubles), loss holds one double per circuit, HVP_OUT_T and
  * HVP_OUT_OMEGA concatenate the circuits' samples; HVP_OUT_ENV and
  * hvp_profile are not available. Circuits with n <= 12 pack 2^(12-n)
- * samples into one shared-memory tile; larger ones run window passes with a
- * per-sample chain of bounded device-side waits (HVP_ETIMEOUT if one
- * expires). hvp_plan_info: info[1] = work items, info[6] = persistent CTAs,
+ * samples into one shared-memory tile; larger ones run window passes of
+ * cfgs[0].window qubits (0 = 12) with a per-sample chain of bounded
+ * device-side waits (HVP_ETIMEOUT if one expires). With HVP_AUTOTUNE in
+ * cfgs[0].flags and a circuit above 12 qubits, the window width is chosen
+ * among 12, 11 and 10 by timing the batch at set-up. hvp_plan_info:
+ * info[1] = work items, info[2] = window qubits, info[6] = persistent CTAs,
  * info[7] = circuits. */
 int hvp_init_batch(hvp_ctx **out, int n_circuits, const hvp_config *cfgs,
                    const double *const *psi_1q, const double *const *ref_data);

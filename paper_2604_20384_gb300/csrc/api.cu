@@ -628,6 +628,8 @@ int hvp_init_batch(hvp_ctx** out, int n_circuits, const hvp_config* cfgs, const 
             return fail(nullptr, HVP_EINVAL, "hvp_init_batch: a circuit above 2^30 amplitudes");
         if (!all_finite(psi_1q[c], (size_t)f.n_samples * f.n * 4)) return fail(nullptr, HVP_ENONFINITE, "psi_1q is not finite");
     }
+    if (cfgs[0].window != 0 && (cfgs[0].window < 6 || cfgs[0].window > 12))
+        return fail(nullptr, HVP_EINVAL, "hvp_init_batch: window must be 0 or 6..12");
     hvp_ctx* c = new (std::nothrow) hvp_ctx();
     if (!c) return fail(nullptr, HVP_ENOMEM, "out of host memory");
     c->cfg = cfgs[0];
@@ -648,7 +650,42 @@ int hvp_init_batch(hvp_ctx** out, int n_circuits, const hvp_config* cfgs, const 
     }
     tiled_set_smem_limits();
     std::string e;
-    int rc = batch_init(&c->batch, n_circuits, cfgs, psi_1q, ref_data, c->stream, e);
+    int window = cfgs[0].window > 0 ? cfgs[0].window : 12;
+    int max_n = 0;
+    for (int i = 0; i < n_circuits; ++i) max_n = std::max(max_n, cfgs[i].n);
+    if ((cfgs[0].flags & HVP_AUTOTUNE) && max_n > 12) {
+        // Autotuning of the window width of the circuits that run window
+        // passes (the number of qubits whose gates are applied per HBM round
+        // trip): build the batch for each candidate, time two calls with
+        // identity gates (the cost of a sweep does not depend on the gate
+        // values) and keep the fastest.
+        std::vector<double> eye(32 * (size_t)c->K, 0.0), res(64 * (size_t)c->K + 2 * n_circuits);
+        for (int k = 0; k < c->K; ++k)
+            for (int d = 0; d < 4; ++d) eye[32 * (size_t)k + 2 * (d * 4 + d)] = 1.0;
+        double best = 1e300;
+        for (int cand : {12, 11, 10}) {
+            BatchImpl* bi = nullptr;
+            std::string e2;
+            if (batch_init(&bi, n_circuits, cfgs, psi_1q, ref_data, c->stream, cand, e2) != HVP_OK) {
+                batch_free(bi);
+                continue;
+            }
+            double* loss = res.data();
+            double* g = loss + n_circuits;
+            double* h = g + 32 * (size_t)c->K;
+            int ok = batch_call(bi, eye.data(), eye.data(), false, loss, g, h, e2);
+            auto t0 = std::chrono::steady_clock::now();
+            for (int r = 0; r < 2 && ok == HVP_OK; ++r) ok = batch_call(bi, eye.data(), eye.data(), false, loss, g, h, e2);
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            batch_free(bi);
+            if (ok == HVP_OK && dt < best) {
+                best = dt;
+                window = cand;
+            }
+        }
+        cudaGetLastError();
+    }
+    int rc = batch_init(&c->batch, n_circuits, cfgs, psi_1q, ref_data, c->stream, window, e);
     if (rc) {
         c->batch = nullptr;
         g_init_error = e;

@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 // ---------------- forward pass p of one sample, all tiles
                 const int p = I.f, s = I.s;
                 const DevPass* P = A.passes + C.pass_ofs + p;
+                const int Lp = 1 << P->w;
                 const E* xin = p == 0 ? nullptr : reinterpret_cast<const E*>(C.ckpt + (size_t)(p - 1) * C.ckpt_stride);
                 E* xout = reinterpret_cast<E*>(C.ckpt + (size_t)p * C.ckpt_stride);
                 stage_pass_mats<TAN>(mats, A, P, 6);
@@ -282,14 +283,14 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 for (int t = 0; t < C.tiles; ++t) {
                     const size_t base = tile_base(P, t, (size_t)s << C.n, P->ng);
                     TileCtx tc{base, P->off_lo, P->off_hi};
-                    if (p == 0) gen_tile<E, kBT>(sf, P, C.psi1q + (size_t)s * C.n * 2, t, P->nq, P->ng, Lt, C.n);
-                    else load_tile<E, kBT, true>(sf, xin, tc, P->in_lo, P->in_hi, Lt);
+                    if (p == 0) gen_tile<E, kBT>(sf, P, C.psi1q + (size_t)s * C.n * 2, t, P->nq, P->ng, Lp, C.n);
+                    else load_tile<E, kBT, true>(sf, xin, tc, P->in_lo, P->in_hi, Lp);
                     __syncthreads();
-                    fwd_gates<TAN>(sf, mats, A, P, 6, Lt);
-                    store_tile<E, kBT>(xout, sf, tc, P->out_lo, P->out_hi, Lt);
+                    fwd_gates<TAN>(sf, mats, A, P, 6, Lp);
+                    store_tile<E, kBT>(xout, sf, tc, P->out_lo, P->out_hi, Lp);
                     if (p == C.P - 1) {   // overlaps at the last cut
                         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        for (int m = tid; m < Lt; m += kBT) {
+                        for (int m = tid; m < Lp; m += kBT) {
                             const unsigned l = __ldg(&P->out_lo[m & 63]) | __ldg(&P->out_hi[m >> 6]);
                             const float2 ph = __ldcg(C.phi + base + __ldg(&P->off_lo[m & 63]) + __ldg(&P->off_hi[m >> 6]));
                             float2 ps, dps = make_float2(0.f, 0.f);
@@ -312,6 +313,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 // ---------------- backward pass p of one sample, all tiles
                 const int p = 2 * C.P - 1 - I.f, s = I.s;
                 const DevPass* P = A.passes + C.pass_ofs + p;
+                const int Lp = 1 << P->w;
                 const E* xin = reinterpret_cast<const E*>(C.ckpt + (size_t)p * C.ckpt_stride);
                 E* co = reinterpret_cast<E*>(C.co);
                 const double2 Ts = __ldcg(C.T + s), Os = __ldcg(C.Om + s);
@@ -323,9 +325,9 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 for (int t = 0; t < C.tiles; ++t) {
                     const size_t base = tile_base(P, t, (size_t)s << C.n, P->ng);
                     TileCtx tc{base, P->off_lo, P->off_hi};
-                    load_tile<E, kBT, true>(sf, xin, tc, P->out_lo, P->out_hi, Lt);
+                    load_tile<E, kBT, true>(sf, xin, tc, P->out_lo, P->out_hi, Lp);
                     if (p == C.P - 1) {
-                        for (int m = tid; m < Lt; m += kBT) {
+                        for (int m = tid; m < Lp; m += kBT) {
                             const unsigned l = __ldg(&P->out_lo[m & 63]) | __ldg(&P->out_hi[m >> 6]);
                             const float2 ph = __ldcg(C.phi + base + __ldg(&P->off_lo[m & 63]) + __ldg(&P->off_hi[m >> 6]));
                             const float2 a = make_float2(Tq.x * ph.x - Tq.y * ph.y, Tq.x * ph.y + Tq.y * ph.x);
@@ -334,11 +336,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                             else sb[swz(l)] = a;
                         }
                     } else {
-                        load_tile<E, kBT, true>(sb, co, tc, P->out_lo, P->out_hi, Lt);
+                        load_tile<E, kBT, true>(sb, co, tc, P->out_lo, P->out_hi, Lp);
                     }
                     __syncthreads();
-                    bwd_gates<TAN>(sf, sb, mats, wred, acc, A, P, 4, Lt);
-                    if (p > 0) store_tile<E, kBT>(co, sb, tc, P->in_lo, P->in_hi, Lt);
+                    bwd_gates<TAN>(sf, sb, mats, wred, acc, A, P, 4, Lp);
+                    if (p > 0) store_tile<E, kBT>(co, sb, tc, P->in_lo, P->in_hi, Lp);
                     __syncthreads();
                 }
                 flush_records<NV>(A, C, P, acc, s);
@@ -437,6 +439,7 @@ struct BatchImpl {
     cudaStream_t stream = nullptr;
     int device = 0;
     int flags = 0;
+    int window = kBTile;        // window qubits of the circuits above kBTile qubits
     std::vector<BCircuit> circ;
     std::vector<int> K, kofs, ns;
     std::vector<void*> allocs;
@@ -577,7 +580,7 @@ int run_batch(BatchImpl* b, bool tan, bool graphs, std::string& err) {
 }  // namespace
 
 int batch_init(BatchImpl** out, int nc, const hvp_config* cfgs, const double* const* psi_1q,
-               const double* const* ref, cudaStream_t stream, std::string& err) {
+               const double* const* ref, cudaStream_t stream, int window, std::string& err) {
     *out = nullptr;
     BatchImpl* b = new BatchImpl();
     auto bail = [&](int rc) { batch_free(b); return rc; };
@@ -594,6 +597,8 @@ int batch_init(BatchImpl** out, int nc, const hvp_config* cfgs, const double* co
     b->stream = stream;
     b->device = cfgs[0].device;
     b->flags = cfgs[0].flags;
+    b->window = window > 0 ? std::min(window, kBTile) : kBTile;
+    if (b->window < 6) { err = "batch: window below 6 qubits"; return bail(HVP_EINVAL); }
     std::vector<Plan> plans(nc);
     std::vector<DevPass> passes;
     std::vector<DevGate> gates;
@@ -610,8 +615,10 @@ int batch_init(BatchImpl** out, int nc, const hvp_config* cfgs, const double* co
         sumK += C.K;
         C.ns_real = cf.n_samples;
         C.packed = cf.n <= kBTile;
-        int rc = make_plan(cf.n, cf.n_layers, std::min(cf.n, kBTile), std::min(kLowBits, std::min(cf.n, kBTile) - 1),
-                           plans[c]);
+        // packed circuits hold all their qubits in one tile; larger ones run
+        // window passes of b->window qubits
+        const int wc = C.packed ? cf.n : std::min(cf.n, b->window);
+        int rc = make_plan(cf.n, cf.n_layers, wc, std::min(kLowBits, wc - 1), plans[c]);
         if (rc) { err = "batch: planning failed for circuit " + std::to_string(c); return bail(rc); }
         const Plan& pl = plans[c];
         C.P = (int)pl.passes.size();
@@ -635,7 +642,7 @@ int batch_init(BatchImpl** out, int nc, const hvp_config* cfgs, const double* co
         } else {
             C.sp = 1;
             C.ns_pad = cf.n_samples;
-            C.tiles = 1 << (cf.n - kBTile);
+            C.tiles = 1 << (cf.n - wc);
             C.slots = cf.n_samples;
             std::vector<DevPass> dp;
             std::vector<DevGate> dg;
@@ -699,7 +706,7 @@ int batch_init(BatchImpl** out, int nc, const hvp_config* cfgs, const double* co
             hvp_config sc = cfgs[c];
             sc.flags = (cfgs[c].flags & HVP_PHI_GIVEN) | HVP_NO_GRAPH;
             sc.precision = HVP_C64;
-            sc.window = 0;   // automatic: min(n, 12), the plan used here
+            sc.window = C.packed ? 0 : b->window;   // the plan used here
             sc.threads = 256;
             sc.variant = 1;
             sc.checkpoint_stride = 0;
@@ -820,7 +827,7 @@ int batch_get(BatchImpl* b, int what, double* out, std::string& err) {
 void batch_info(const BatchImpl* b, long long* info) {
     info[0] = b->sumK;
     info[1] = b->n_items;
-    info[2] = kBTile;
+    info[2] = b->window;
     info[3] = 1;
     info[4] = b->launches;
     info[5] = (long long)(b->bytes >> 20);

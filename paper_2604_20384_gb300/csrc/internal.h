@@ -160,7 +160,7 @@ struct BatchImpl;
 
 namespace hvp {
 int batch_init(BatchImpl** out, int n_circuits, const hvp_config* cfgs, const double* const* psi_1q,
-               const double* const* ref, cudaStream_t stream, std::string& err);
+               const double* const* ref, cudaStream_t stream, int window, std::string& err);
 int batch_call(BatchImpl* b, const double* G, const double* V, bool dev, double* loss, double* grad, double* hvp,
                std::string& err);
 int batch_get(BatchImpl* b, int what, double* out, std::string& err);

@@ -252,11 +252,13 @@ class BatchContext(Context):
     """
 
     def __init__(self, circuits, *, riemannian: bool = False, phi_given: bool = False, graphs: bool = True,
-                 frobenius: bool = False, device: int = 0, stream: int | None = None):
+                 frobenius: bool = False, window: int = 0, autotune: bool = False, device: int = 0,
+                 stream: int | None = None):
         self._lib = load()
         nc = len(circuits)
         flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
-                 | (0 if graphs else HVP_NO_GRAPH) | (HVP_FROBENIUS if frobenius else 0))
+                 | (0 if graphs else HVP_NO_GRAPH) | (HVP_FROBENIUS if frobenius else 0)
+                 | (HVP_AUTOTUNE if autotune else 0))
         cfgs = (HVPConfig * nc)()
         self._keep = []
         psis = (_dp * nc)()
@@ -264,7 +266,7 @@ class BatchContext(Context):
         self.Ks, self.ns = [], []
         for c, (n, L, psi1q, ref) in enumerate(circuits):
             psi1q = np.asarray(psi1q)
-            cfgs[c] = HVPConfig(n, L, int(psi1q.shape[0]), HVP_C64, flags, 0, 0, 0, 0, device, stream)
+            cfgs[c] = HVPConfig(n, L, int(psi1q.shape[0]), HVP_C64, flags, 0, window, 0, 0, device, stream)
             a, r = _f64(psi1q), _f64(ref)
             self._keep += [a, r]
             psis[c] = _ptr(a)
@@ -327,6 +329,6 @@ class BatchContext(Context):
     def plan_info(self) -> dict:
         info = (ctypes.c_longlong * 10)()
         self._check(self._lib.hvp_plan_info(self._h, info))
-        keys = ["K", "items", "tile_bits", "checkpoint_stride", "launches_per_hvp", "device_mib", "ctas",
+        keys = ["K", "items", "window", "checkpoint_stride", "launches_per_hvp", "device_mib", "ctas",
                 "circuits", "threads", "variant"]
         return dict(zip(keys, list(info)))

@@ -38,6 +38,26 @@ def test_small_uneven_batch_matches_oracle(riemannian, graphs):
         assert rel(g2[i], o[kg]) < TOL
 
 
+@pytest.mark.parametrize("window,autotune", [(10, False), (0, True)])
+def test_batch_window_widths_and_autotune(window, autotune):
+    # circuits above 12 qubits run window passes of `window` qubits (or the
+    # autotuned width); results must not depend on it
+    ws, circuits = _small_batch()
+    with native.BatchContext(circuits, window=window, autotune=autotune) as b:
+        info = b.plan_info()
+        loss, grads, hvps = b.hvp([w.G for w in ws], [w.V for w in ws])
+    if window:
+        assert info["window"] == window
+    else:
+        assert info["window"] in (10, 11, 12)
+    for i, w in enumerate(ws):
+        phi = oracle.reference_states(w.n, w.n_layers, w.Uref, w.psi1q)
+        o = oracle.evaluate(w.n, w.n_layers, w.G, w.V, w.psi1q, phi)
+        assert abs((1 - loss[i]) - (1 - o["loss"])) <= TOL * (1 - o["loss"]) + 1e-13, i
+        assert rel(grads[i], o["grad"]) < TOL, (i, rel(grads[i], o["grad"]))
+        assert rel(hvps[i], o["hvp"]) < TOL, (i, rel(hvps[i], o["hvp"]))
+
+
 def test_full_uneven_batch_matches_single_contexts():
     # 64 circuits, n ~ U{8..16}, L ~ U{4..20}, N_s log-uniform in [32, 512]
     shapes = uneven_batch_shapes(64, seed=0)
