@@ -44,15 +44,19 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic():
+def recorded_traffic(info):
     """DRAM bytes per backward-kernel launch from the committed ncu capture, if
-    it was taken on the current kernel sources (else None)."""
+    it was taken on the current kernel sources and the same plan (window,
+    threads, arithmetic), else None."""
     try:
         with open(TRAFFIC_FILE) as f:
             doc = json.load(f)
     except (OSError, ValueError):
         return None
     if doc.get("source_sha256") != kernel_source_hash():
+        return None
+    plan = doc.get("plan", {})
+    if any(plan.get(k) != info[k] for k in ("window", "threads", "variant")):
         return None
     return doc.get("bwd_kernel_bytes_per_launch")
 
@@ -183,7 +187,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
     ap.add_argument("--variant", type=int, default=0, help="1 scalar FMA, 2 packed FMA (0 = library default)")
     ap.add_argument("--window", type=int, default=0, help="window qubits (0 = library default)")
-    ap.add_argument("--autotune", action="store_true", help="let the library autotune at set-up")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library defaults (or --threads/--variant/--window) instead of autotuning at set-up")
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (for profiler captures)")
     args = ap.parse_args()
@@ -213,10 +218,11 @@ def main():
     dev = torch.device("cuda", local)
 
     w = make_workload(**dict(WORKLOAD, n_samples=args.samples))
+    autotune = not (args.no_autotune or args.threads or args.variant or args.window)
     stream = torch.cuda.Stream(device=dev)
     ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
                          stream=stream.cuda_stream, threads=args.threads, variant=args.variant,
-                         window=args.window, autotune=args.autotune)
+                         window=args.window, autotune=autotune)
     K = w.K
     G_dev = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
     V_dev = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
@@ -313,8 +319,10 @@ def main():
     all_ms = sum(by_kind[k]["ms"] for k in by_kind if k.startswith("pass_"))
     all_fl = sum(by_kind[k]["flops"] for k in by_kind if k.startswith("pass_"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": recorded_traffic(),
-                "kernel": "tiled_bwd_kernel<tangent,scalar,256> (backward and turnaround window passes)",
+                "frac": achieved / alu_peak, "traffic": recorded_traffic(info),
+                "kernel": f"tiled_bwd_kernel<tangent, {'packed' if info['variant'] == 2 else 'scalar'}, "
+                          f"{info['threads']} threads> (backward and turnaround window passes, "
+                          f"window {info['window']})",
                 "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
                 "algorithmic_bytes_per_launch": p_by / p_n,
                 "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
@@ -333,7 +341,8 @@ def main():
             "data": "synthetic (seeded Haar brickwall, Haar product states)",
             "config": {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152), complex64 window passes, "
                                    "FP64 accumulation", "n": 20, "L": 16, "N_s": 64, "K": K,
-                       "window": info["window"], "passes": info["passes"],
+                       "window": info["window"], "passes": info["passes"], "threads": info["threads"],
+                       "variant": info["variant"], "autotuned": autotune,
                        "checkpoint_stride": info["checkpoint_stride"], "tiles_per_cta": info["tiles_per_cta"],
                        "l2": "inputs larger than L2 (512 MiB per state set, 129 MB L2)",
                        "parallelism": f"replicas x{world}"},

@@ -79,7 +79,8 @@ typedef struct {
                               passes, the others recomputed; 0 = automatic     */
     int window;            /* local qubits per shared-memory tile; 0 = auto    */
     int threads;           /* threads per CTA of the window-pass kernels,
-                              256 or 512; 0 = auto                             */
+                              128 (scalar arithmetic, two CTAs per SM when
+                              the tiles fit), 256 or 512; 0 = auto             */
     int variant;           /* arithmetic of the window-pass kernels: 1 scalar
                               FP32 FMA, 2 packed fma.rn.f32x2, 3 scalar with
                               two groups per thread iteration in the backward

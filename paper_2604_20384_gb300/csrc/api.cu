@@ -12,6 +12,7 @@
 // others are recomputed segment by segment before the backward passes need
 // them.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -374,9 +375,11 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
     if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))
         return fail(c, HVP_EINVAL, "window must be 0 (auto) or in [6, 12]");
-    if (cfg->threads != 0 && cfg->threads != 256 && cfg->threads != 512)
-        return fail(c, HVP_EINVAL, "threads must be 0 (auto), 256 or 512");
+    if (cfg->threads != 0 && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512)
+        return fail(c, HVP_EINVAL, "threads must be 0 (auto), 128, 256 or 512");
     if (cfg->variant < 0 || cfg->variant > 3) return fail(c, HVP_EINVAL, "variant must be 0 (auto), 1, 2 or 3");
+    if (cfg->threads == 128 && cfg->variant > 1)
+        return fail(c, HVP_EINVAL, "128 threads run the scalar arithmetic (variant 0 or 1) only");
     if (((size_t)1 << n) * (size_t)ns > ((size_t)1 << 34))
         return fail(c, HVP_EINVAL, "2^n * n_samples above 2^34 amplitudes");
     if (!all_finite(psi_1q, (size_t)ns * n * 4)) return fail(c, HVP_ENONFINITE, "psi_1q is not finite");
@@ -412,29 +415,36 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         for (int k = 0; k < c->K; ++k)
             for (int d = 0; d < 4; ++d) eye[32 * (size_t)k + 2 * (d * 4 + d)] = 1.0;
         double best = 1e300;
-        for (int wdw : windows)
-            for (int var : {1, 2, 3}) {
-                hvp_config sc = *cfg;
-                sc.flags &= ~HVP_AUTOTUNE;
-                sc.window = wdw >= n ? 0 : wdw;
-                sc.threads = 256;
-                sc.variant = var;
-                hvp_ctx* tmp = nullptr;
-                if (hvp_init(&tmp, &sc, psi_1q, ref) != HVP_OK) continue;
-                double loss = 0.0;
-                int ok = hvp_hvp(tmp, eye.data(), eye.data(), &loss, res_g.data(), res_h.data());
-                auto t0 = std::chrono::steady_clock::now();
-                for (int r = 0; r < 2 && ok == HVP_OK; ++r)
-                    ok = hvp_hvp(tmp, eye.data(), eye.data(), &loss, res_g.data(), res_h.data());
-                const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-                hvp_free(tmp);
-                if (ok == HVP_OK && dt < best) {
-                    best = dt;
-                    tuned.window = sc.window;
-                    tuned.threads = 256;
-                    tuned.variant = var;
-                }
+        // candidates: (window, threads, arithmetic); 128-thread CTAs pair up
+        // on one SM when the window's tiles leave room in shared memory
+        std::vector<std::array<int, 3>> cands;
+        for (int wdw : windows) {
+            for (int var : {1, 2, 3}) cands.push_back({wdw, 256, var});
+            if (wdw <= 11) cands.push_back({wdw, 128, 1});
+        }
+        for (const auto& cand : cands) {
+            const int wdw = cand[0], var = cand[2];
+            hvp_config sc = *cfg;
+            sc.flags &= ~HVP_AUTOTUNE;
+            sc.window = wdw >= n ? 0 : wdw;
+            sc.threads = cand[1];
+            sc.variant = var;
+            hvp_ctx* tmp = nullptr;
+            if (hvp_init(&tmp, &sc, psi_1q, ref) != HVP_OK) continue;
+            double loss = 0.0;
+            int ok = hvp_hvp(tmp, eye.data(), eye.data(), &loss, res_g.data(), res_h.data());
+            auto t0 = std::chrono::steady_clock::now();
+            for (int r = 0; r < 2 && ok == HVP_OK; ++r)
+                ok = hvp_hvp(tmp, eye.data(), eye.data(), &loss, res_g.data(), res_h.data());
+            const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            hvp_free(tmp);
+            if (ok == HVP_OK && dt < best) {
+                best = dt;
+                tuned.window = sc.window;
+                tuned.threads = sc.threads;
+                tuned.variant = var;
             }
+        }
         cudaGetLastError();
     }
 

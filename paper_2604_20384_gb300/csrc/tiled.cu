@@ -37,7 +37,7 @@ using namespace tile;
 
 // ------------------------------------------------------------ forward kernel
 template <bool TAN, bool P2, int NT>
-__global__ void __launch_bounds__(NT, 2) tiled_fwd_kernel(TiledArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
     using MT = typename Math<P2>::M;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT, 2) tiled_fwd_kernel(TiledArgs a) {
 
 // ----------------------------------------------------------- backward kernel
 template <bool TAN, bool P2, int NT, bool G2 = false>
-__global__ void __launch_bounds__(NT, 1) tiled_bwd_kernel(TiledArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 128 ? 2 : 1) tiled_bwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
     using MT = typename Math<P2>::M;
     constexpr int NW = NT / 32;
@@ -208,6 +208,7 @@ cudaError_t tiled_set_smem_limits() {
 #define HVP_SET(T, P, N) if ((e = set_limits_one<T, P, N>()) != cudaSuccess) return e
     HVP_SET(true, false, 256); HVP_SET(true, false, 512); HVP_SET(true, true, 256); HVP_SET(true, true, 512);
     HVP_SET(false, false, 256); HVP_SET(false, false, 512); HVP_SET(false, true, 256); HVP_SET(false, true, 512);
+    HVP_SET(true, false, 128); HVP_SET(false, false, 128);
 #undef HVP_SET
     return cudaSuccess;
 }
@@ -221,14 +222,17 @@ cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, i
     dim3 grid(a.cx_count, a.n_samples);
 #define HVP_L(K, T, P, N) K<T, P, N><<<grid, N, smem, st>>>(a)
 #define HVP_PICK(K)                                                                                  \
-    if (tangent) {                                                                                   \
+    if (threads == 128) {                                                                            \
+        if (tangent) HVP_L(K, true, false, 128); else HVP_L(K, false, false, 128);                   \
+    } else if (tangent) {                                                                            \
         if (p2) { if (threads == 512) HVP_L(K, true, true, 512); else HVP_L(K, true, true, 256); }    \
         else { if (threads == 512) HVP_L(K, true, false, 512); else HVP_L(K, true, false, 256); }     \
     } else {                                                                                         \
         if (p2) { if (threads == 512) HVP_L(K, false, true, 512); else HVP_L(K, false, true, 256); }  \
         else { if (threads == 512) HVP_L(K, false, false, 512); else HVP_L(K, false, false, 256); }   \
     }
-    if (threads != 256 && threads != 512) return cudaErrorInvalidValue;
+    if (threads != 128 && threads != 256 && threads != 512) return cudaErrorInvalidValue;
+    if (threads == 128 && variant != 1) return cudaErrorInvalidValue;
     if (bwd && variant == 3) {
         if (tangent) {
             if (threads == 512) tiled_bwd_kernel<true, false, 512, true><<<grid, 512, smem, st>>>(a);

@@ -84,6 +84,11 @@ def test_init_validates_arguments_before_cuda():
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
     cfg = native.HVPConfig(6, 3, 2, 0, 1 << 10, 0, 0, 0, 0, 0, None)    # unknown flag
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
+    cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 192, 0, 0, None)        # unsupported thread count
+    assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
+    cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 128, 2, 0, None)        # 128 threads: scalar arithmetic only
+    assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
+    assert b"128 threads" in lib.hvp_last_error(None)
     cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 0, 0, 0, None)
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), None, native._ptr(ref)) == native.HVP_EINVAL
     bad = psi.copy()
