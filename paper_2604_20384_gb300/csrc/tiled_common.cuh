@@ -195,13 +195,22 @@ __device__ __forceinline__ void stage_mats(typename Math<P2>::M* __restrict__ ds
 }
 
 // One forward gate over all groups of the tile.
-// MA: matrix accessor, a pointer into shared memory or an object whose
-// operator[] reads another state space (e.g. constant memory).
+// MA: matrix accessor (a pointer into shared memory, or any type with
+// operator[] returning a matrix element).
 template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*>
-__device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, MA Gm, MA Vm, int u, int v,
+__device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, MA Gm_s, MA Vm_s, int u, int v,
                                          int Lt) {
     const int plo = min(u, v), phi_ = max(u, v);
     const unsigned mu = 1u << u, mv = 1u << v;
+    // The gate's matrices are read from shared memory once per thread and
+    // kept in registers for all of the thread's groups.
+    using MT = typename Math<P2>::M;
+    MT Gm[16], Vm[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        Gm[e] = Gm_s[e];
+        if constexpr (TAN) Vm[e] = Vm_s[e];
+    }
     for (int q = threadIdx.x; q < (Lt >> 2); q += NT) {
         const unsigned l0 = insert0(insert0(q, plo), phi_);
         const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
