@@ -100,6 +100,92 @@ static bool simulate(int K, int b, const std::vector<int>& fq, const std::vector
     return true;
 }
 
+// Beam search over window positions. A step moves to a window [lo, lo+w-1]
+// that shares >= b qubits with the current one and applies every gate that
+// is ready inside it (none: a transit pass). The cost of a plan is its
+// number of passes, a step with more than kMaxGatesPerPass gates counting as
+// several. Each round keeps the `width` cheapest partial plans (most gates
+// applied first among equal costs), one per (applied set, window).
+static bool beam_plan(int n, int w, int b, const std::vector<int>& fq, const std::vector<int>& p1,
+                      const std::vector<int>& p2, std::vector<std::pair<Window, std::vector<int>>>& out) {
+    const int K = (int)fq.size();
+    const int nw = n - w + 1;
+    const size_t width = 64;
+    struct Node {
+        int cost = 0, ndone = 0, lo = 0;
+        std::vector<char> done;
+        std::vector<std::pair<int, std::vector<int>>> hist;
+    };
+    auto step = [&](const Node& from, int lo, Node& to) {
+        to.done = from.done;
+        to.hist = from.hist;
+        std::vector<int> list;
+        for (int g = 0; g < K; ++g) {
+            if (to.done[g] || fq[g] < lo || fq[g] + 1 > lo + w - 1) continue;
+            if ((p1[g] >= 0 && !to.done[p1[g]]) || (p2[g] >= 0 && !to.done[p2[g]])) continue;
+            to.done[g] = 1;
+            list.push_back(g);
+        }
+        const int c = (int)list.size();
+        to.cost = from.cost + (c == 0 ? 1 : (c + kMaxGatesPerPass - 1) / kMaxGatesPerPass);
+        to.ndone = from.ndone + c;
+        to.lo = lo;
+        to.hist.emplace_back(lo, std::move(list));
+    };
+    auto better = [](const Node& x, const Node& y) {
+        return x.cost != y.cost ? x.cost < y.cost : x.ndone > y.ndone;
+    };
+    std::vector<Node> cur;
+    Node root;
+    root.done.assign(K, 0);
+    for (int lo = 0; lo < nw; ++lo) {
+        Node nd;
+        step(root, lo, nd);
+        if (nd.ndone > 0) cur.push_back(std::move(nd));
+    }
+    bool found = false;
+    Node best;
+    for (int round = 0; round < 8 * K + 8 && !cur.empty(); ++round) {
+        std::vector<Node> next;
+        for (const Node& nd : cur) {
+            if (nd.ndone == K) {
+                if (!found || nd.cost < best.cost) { best = nd; found = true; }
+                continue;
+            }
+            if (found && nd.cost + 1 >= best.cost) continue;
+            for (int lo = 0; lo < nw; ++lo) {
+                if (lo == nd.lo || overlap({nd.lo, nd.lo + w - 1}, {lo, lo + w - 1}) < b) continue;
+                Node nx;
+                step(nd, lo, nx);
+                next.push_back(std::move(nx));
+            }
+        }
+        std::sort(next.begin(), next.end(), better);
+        cur.clear();
+        std::vector<std::pair<int, std::vector<char>>> seen;
+        for (Node& nd : next) {
+            if (cur.size() >= width) break;
+            bool dup = false;
+            for (const auto& sv : seen)
+                if (sv.first == nd.lo && sv.second == nd.done) { dup = true; break; }
+            if (dup) continue;
+            seen.emplace_back(nd.lo, nd.done);
+            cur.push_back(std::move(nd));
+        }
+    }
+    if (!found) return false;
+    out.clear();
+    for (auto& h : best.hist) out.emplace_back(Window{h.first, h.first + w - 1}, std::move(h.second));
+    return true;
+}
+
+static int passes_after_split(const std::vector<std::pair<Window, std::vector<int>>>& v) {
+    int P = 0;
+    for (const auto& pr : v)
+        P += pr.second.empty() ? 1 : (int)((pr.second.size() + kMaxGatesPerPass - 1) / kMaxGatesPerPass);
+    return P;
+}
+
 int make_plan(int n, int L, int w, int b, Plan& plan) {
     if (n < 2 || n > kMaxN || L < 1 || w < 2 || w > kMaxW || b < 1 || b >= w) return HVP_EINVAL;
     plan = Plan();
@@ -116,12 +202,11 @@ int make_plan(int n, int L, int w, int b, Plan& plan) {
     }
 
     std::vector<Window> wins;
-    std::vector<std::pair<int, std::vector<int>>> best;
+    std::vector<std::pair<Window, std::vector<int>>> best;
     if (n <= w) {
-        wins.push_back({0, n - 1});
         std::vector<int> all(K);
         for (int k = 0; k < K; ++k) all[k] = k;
-        best.emplace_back(0, all);
+        best.emplace_back(Window{0, n - 1}, all);
     } else {
         const int m = (n - b + (w - b) - 1) / (w - b);  // windows with overlaps >= b
         for (int j = 0; j < m; ++j) {
@@ -141,14 +226,21 @@ int make_plan(int n, int L, int w, int b, Plan& plan) {
         for (auto& s : seqs) {
             std::vector<std::pair<int, std::vector<int>>> cand;
             if (!simulate(K, b, fq, p1, p2, wins, s, cand)) continue;
-            if (!ok || cand.size() < best.size()) { best = cand; ok = true; }
+            std::vector<std::pair<Window, std::vector<int>>> cw;
+            for (auto& pr : cand) cw.emplace_back(wins[pr.first], std::move(pr.second));
+            if (!ok || passes_after_split(cw) < passes_after_split(best)) { best = std::move(cw); ok = true; }
+        }
+        std::vector<std::pair<Window, std::vector<int>>> bw;
+        if (beam_plan(n, w, b, fq, p1, p2, bw) && (!ok || passes_after_split(bw) < passes_after_split(best))) {
+            best = std::move(bw);
+            ok = true;
         }
         if (!ok) return HVP_EINVAL;
     }
 
     // Split passes over the shared-memory gate budget (a prefix of a valid
     // pass order is itself valid).
-    std::vector<std::pair<int, std::vector<int>>> split;
+    std::vector<std::pair<Window, std::vector<int>>> split;
     for (auto& pr : best) {
         if (pr.second.empty()) split.push_back(pr);
         for (size_t s = 0; s < pr.second.size(); s += kMaxGatesPerPass) {
@@ -163,13 +255,13 @@ int make_plan(int n, int L, int w, int b, Plan& plan) {
     // with the next window first (they land on the lowest address bits).
     auto window_qubits = [&](int p) {
         std::vector<int> q;
-        for (int x = wins[split[p].first].lo; x <= wins[split[p].first].hi; ++x) q.push_back(x);
+        for (int x = split[p].first.lo; x <= split[p].first.hi; ++x) q.push_back(x);
         return q;
     };
     auto ordered_for_next = [&](int p) {
         std::vector<int> cur = window_qubits(p), first, rest;
         if (p + 1 < P) {
-            const Window& nx = wins[split[p + 1].first];
+            const Window& nx = split[p + 1].first;
             for (int q : cur) (in_window(nx, q) ? first : rest).push_back(q);
         } else {
             first = cur;
@@ -195,7 +287,7 @@ int make_plan(int n, int L, int w, int b, Plan& plan) {
         pp.gates = split[p].second;
         for (int g : pp.gates) plan.pass_of_gate[g] = p;
         pp.pos_in = pos;
-        if (n > w && p + 1 < P && split[p + 1].first != split[p].first) {
+        if (n > w && p + 1 < P && split[p + 1].first.lo != split[p].first.lo) {
             std::vector<int> B;
             for (int q : wq) B.push_back(pos[q]);
             std::sort(B.begin(), B.end());

@@ -228,7 +228,7 @@ def test_headline_shape_sampled_against_oracle(threads, window):
     # linearity in the samples.
     w = make_workload(20, 16, 64, seed=0)
     with native.Context(20, 16, w.psi1q, w.Uref, threads=threads, window=window) as ctx:
-        assert ctx.plan_info()["passes"] == (5 if window == 0 else 7)
+        assert ctx.plan_info()["passes"] == (4 if window == 0 else 6)
         loss, grad, hvp = ctx.hvp(w.G, w.V)
         T, Om = ctx.get("T"), ctx.get("Omega")
         E, DE = ctx.get("env")
