@@ -55,10 +55,11 @@ def recorded_traffic(info):
         return None
     if doc.get("source_sha256") != kernel_source_hash():
         return None
-    plan = doc.get("plan", {})
-    if any(plan.get(k) != info[k] for k in ("window", "threads", "variant")):
-        return None
-    return doc.get("bwd_kernel_bytes_per_launch")
+    for rec in doc.get("records", []):
+        plan = rec.get("plan", {})
+        if all(plan.get(k) == info[k] for k in ("window", "threads", "variant", "passes")):
+            return rec.get("bwd_kernel_bytes_per_launch")
+    return None
 
 
 def _peaks():
