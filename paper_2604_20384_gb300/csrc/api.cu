@@ -355,8 +355,14 @@ int compute_phi_from_uref(hvp_ctx* c, const double* uref) {
 int choose_tiling(hvp_ctx* c) {
     const int ns = c->cfg.n_samples;
     const long long tps = 1ll << (c->cfg.n - c->w);
+    // About 16 waves of resident CTAs (one per SM at 256 or 512 threads, two
+    // at 128): the last, partly filled wave then costs a few percent of a
+    // launch at most (measured on GB300 at n = 20, N_s = 64: 8 waves 97.3 ms,
+    // 16 waves 94.6 ms, 32 waves 94.8 ms per evaluation). More CTAs per
+    // sample also means more FP64 environment records to reduce.
+    const long long per_sm = c->threads <= 128 ? 2 : 1;
     long long cx = 1;
-    while (cx < tps && cx * ns < 8 * 152) cx *= 2;
+    while (cx < tps && cx * ns < 16 * 152 * per_sm) cx *= 2;
     c->cx_count = (int)cx;
     c->tiles_per_cta = (int)(tps / cx);
     return HVP_OK;
