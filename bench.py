@@ -137,9 +137,10 @@ def cpu_baseline(w, steps=1, warmup=0, max_seconds=150.0):
     phi = oracle.reference_states(w.n, w.n_layers, w.Uref, sub)
     stride = max(1, int(round(w.K ** 0.5)))
     times = []
+    out = None
     for i in range(warmup + steps):
         t0 = time.perf_counter()
-        oracle.evaluate(w.n, w.n_layers, w.G, w.V, sub, phi, threads=m, ckpt_stride=stride)
+        out = oracle.evaluate(w.n, w.n_layers, w.G, w.V, sub, phi, threads=m, ckpt_stride=stride, want_env=True)
         dt = time.perf_counter() - t0
         if i >= warmup:
             times.append(dt)
@@ -149,7 +150,7 @@ def cpu_baseline(w, steps=1, warmup=0, max_seconds=150.0):
     return dict(value=(m / w.n_samples) / sec, unit="HVPs/s", cores=m, kind="oracle",
                 sample=f"{m} of {w.n_samples} samples (n={w.n}, L={w.n_layers}), {m} threads, "
                        f"checkpoint stride {stride}; {sec:.2f} s per sample batch, scaled by {m}/{w.n_samples}",
-                seconds_per_step=sec, steps=len(times))
+                seconds_per_step=sec, steps=len(times), oracle_out=out)
 
 
 def run_reference(args, rank, world):
@@ -295,6 +296,10 @@ def main():
            "d2h_bytes_per_step": res_doubles * 8 + 4, "ms_per_step": e2e_ms}
 
     # ------------------------------------------- per-launch roofline (events)
+    # per-sample outputs of the last (host-array) call, for the parity check
+    T_gpu, Om_gpu = ctx.get("T"), ctx.get("Omega")
+    E_gpu, DE_gpu = ctx.get("env")
+
     prof = ctx.profile(G_dev.data_ptr(), V_dev.data_ptr())
     kinds = prof["kind"]
     by_kind = {}
@@ -400,7 +405,20 @@ def main():
             "achieved_tflops": amp_gates * 384 / (b_ms / 1e3) / 1e12}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(w).items() if k not in ("seconds_per_step", "steps")}
+        cb = cpu_baseline(w)
+        line["cpu_baseline"] = {k: v for k, v in cb.items() if k not in ("seconds_per_step", "steps", "oracle_out")}
+        # Parity of the timed configuration against the same oracle run, on the
+        # samples it covered: per-sample overlaps and environments (the
+        # sample-summed outputs are linear in them).
+        o, m = cb["oracle_out"], cb["cores"]
+
+        def _rel(a, b):
+            return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+        line["parity_vs_oracle"] = {
+            "samples": m, "tolerance": 1e-5,
+            "T_rel": _rel(T_gpu[:m], o["T"]), "Omega_rel": _rel(Om_gpu[:m], o["Omega"]),
+            "E_rel": _rel(E_gpu[:m], o["E"]), "DE_rel": _rel(DE_gpu[:m], o["DE"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
