@@ -1,6 +1,6 @@
 """Builds the FP64 oracle shared library (plain C, gcc).
 
-Test infrastructure only: the oracle is the checker of the CUDA library, not
+Test infrastructure only: the oracle is the reference the CUDA library is tested against, not
 part of it. Contraction of a*b+c into fused multiply-adds is switched off so
 that the oracle rounds the same way on x86-64 and on aarch64.
 """

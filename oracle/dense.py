@@ -1,4 +1,4 @@
-"""Dense brute-force checker for tiny n (test infrastructure only).
+"""Dense brute-force evaluation for tiny n (test infrastructure only).
 
 It shares nothing with oracle.c: it builds the full 2^n x 2^n brickwall
 unitary from Kronecker products of layer operators and obtains every

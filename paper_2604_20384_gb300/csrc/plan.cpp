@@ -104,7 +104,7 @@ static bool simulate(int K, int b, const std::vector<int>& fq, const std::vector
 // that shares >= b qubits with the current one and applies every gate that
 // is ready inside it (none: a transit pass). The cost of a plan is its
 // number of passes, a step with more than kMaxGatesPerPass gates counting as
-// several. Each round keeps the `width` cheapest partial plans (most gates
+// several. Each step keeps the `width` cheapest partial plans (most gates
 // applied first among equal costs), one per (applied set, window).
 static bool beam_plan(int n, int w, int b, const std::vector<int>& fq, const std::vector<int>& p1,
                       const std::vector<int>& p2, std::vector<std::pair<Window, std::vector<int>>>& out) {
@@ -145,7 +145,7 @@ static bool beam_plan(int n, int w, int b, const std::vector<int>& fq, const std
     }
     bool found = false;
     Node best;
-    for (int round = 0; round < 8 * K + 8 && !cur.empty(); ++round) {
+    for (int it = 0; it < 8 * K + 8 && !cur.empty(); ++it) {
         std::vector<Node> next;
         for (const Node& nd : cur) {
             if (nd.ndone == K) {
