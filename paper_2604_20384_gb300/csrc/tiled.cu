@@ -11,7 +11,8 @@
 //   backward gate k, with a = phi^[K-k] and b = dphi^[K-k] before the update
 //   (Eq. environment, Eq. Dpsi, Eq. bis, Eq. dbis):
 //       psi^[k-1]  = G_k^-1 psi^[k]
-//       dpsi^[k-1] = G_k^-1 (dpsi^[k] - V_k psi^[k-1])
+//       dpsi^[k-1] = G_k^-1 dpsi^[k] - Y_k psi^[k],  Y_k = G_k^-1 V_k G_k^-1
+//                    (= G_k^-1 (dpsi^[k] - V_k psi^[k-1]))
 //       E_k  += sum_a conj(a_i) psi^[k-1]_j
 //       DE_k += sum_a conj(b_i) psi^[k-1]_j + conj(a_i) dpsi^[k-1]_j
 //       b <- G_k^dag b + V_k^dag a ,  a <- G_k^dag a
@@ -19,11 +20,14 @@
 // boundaries it comes from the forward checkpoint, so recomputation error does
 // not build up over the whole circuit.
 //
-// Two kernels: a forward-only kernel (small register footprint, two CTAs per
-// SM) and a backward kernel (forward part of the turnaround pass included).
-// Two arithmetic forms, chosen at run time: scalar FP32 FMAs, or packed
-// fma.rn.f32x2 with gate matrices pre-expanded to {m.re, m.re, -m.im, m.im}
-// so that one complex multiply-add is two packed FMAs.
+// Two kernels: a forward-only kernel (small register footprint: two CTAs per
+// SM at 256 threads, four at 128) and a backward kernel (forward part of the
+// turnaround pass included; 255 registers: one CTA per SM at 256 threads,
+// two at 128). Arithmetic forms, chosen at run time: scalar FP32 FMAs
+// (variant 1), packed fma.rn.f32x2 with gate matrices pre-expanded to
+// {m.re, m.re, -m.im, m.im} so that one complex multiply-add is two packed
+// FMAs (variant 2), or scalar with two groups per thread iteration in the
+// backward pass (variant 3).
 //
 // Environment sums: per thread in FP32 over its groups of four amplitudes,
 // a warp reduce-scatter (each lane ends with two of the 64 real components),
