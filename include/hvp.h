@@ -122,6 +122,16 @@ int hvp_init(hvp_ctx **out, const hvp_config *cfg, const double *psi_1q,
 int hvp_init_batch(hvp_ctx **out, int n_circuits, const hvp_config *cfgs,
                    const double *const *psi_1q, const double *const *ref_data);
 
+/* Test of the batch kernel's bounded device-side waits (no counterpart in the
+ * paper). dep_bias = 1 makes every per-sample chain wait ask for one more
+ * finished phase than can finish, so the first wait gives up after
+ * spin_limit sleeps of 200 ns, every later wait gives up at once, and the
+ * next call returns HVP_ETIMEOUT; the context stays usable. dep_bias = 0 with
+ * spin_limit = 20000000 restores the normal waits. Applies to the next calls
+ * (captured graphs are rebuilt). HVP_EINVAL if ctx is not a batch context,
+ * dep_bias is not 0 or 1 or spin_limit < 1. */
+int hvp_batch_wait_test(hvp_ctx *ctx, int dep_bias, long long spin_limit);
+
 /* Loss and gradient (Alg. 1 without tangents, Alg. 2 first two steps).
  *   G    : host, K*32 doubles.
  *   loss : host, 1 double (may be NULL).

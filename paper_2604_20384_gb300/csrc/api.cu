@@ -835,6 +835,14 @@ int hvp_plan_info(const hvp_ctx* c, long long info[10]) {
     return HVP_OK;
 }
 
+int hvp_batch_wait_test(hvp_ctx* c, int dep_bias, long long spin_limit) {
+    if (!c) return fail(nullptr, HVP_EINVAL, "hvp_batch_wait_test: ctx is NULL");
+    if (!c->batch) return fail(c, HVP_EINVAL, "hvp_batch_wait_test: not a batch context");
+    if (dep_bias < 0 || dep_bias > 1 || spin_limit < 1)
+        return fail(c, HVP_EINVAL, "hvp_batch_wait_test: dep_bias must be 0 or 1 and spin_limit >= 1");
+    return batch_wait_test(c->batch, dep_bias, spin_limit);
+}
+
 void hvp_free(hvp_ctx* c) {
     if (!c) return;
     if (c->batch) {

@@ -67,6 +67,7 @@ struct BatchArgs {
     int* done;
     int* error;
     long long spin_limit;
+    int dep_bias;       // added to every awaited count (0; 1 in the expired-wait test)
     int frob;           // Frobenius cost: co-state weights (1, 0) instead of (T_s, Omega_s)
 };
 
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_kernel(BatchArgs A) {
                 volatile int* d = A.done + C.done_ofs + I.s;
                 long long spins = 0;
                 volatile int* errflag = A.error;
-                while (*d < I.dep) {
+                while (*d < I.dep + A.dep_bias) {
                     __nanosleep(200);
                     // bounded wait: report and move on; after the first expired
                     // wait every later wait gives up at once
@@ -440,6 +441,8 @@ struct BatchImpl {
     int device = 0;
     int flags = 0;
     int window = kBTile;        // window qubits of the circuits above kBTile qubits
+    long long spin_limit = 20000000;   // x 200 ns sleeps: a few seconds at most
+    int dep_bias = 0;
     std::vector<BCircuit> circ;
     std::vector<int> K, kofs, ns;
     std::vector<void*> allocs;
@@ -539,7 +542,8 @@ int enqueue_batch(BatchImpl* b, bool tan, std::string& err) {
     A.ticket = b->d_sync;
     A.error = b->d_sync + 1;
     A.done = b->d_sync + 2;
-    A.spin_limit = 20000000;   // x 200 ns sleeps: a few seconds at most
+    A.spin_limit = b->spin_limit;
+    A.dep_bias = b->dep_bias;
     A.frob = (b->flags & HVP_FROBENIUS) ? 1 : 0;
     const size_t smem = batch_smem(tan);
     if (tan) batch_kernel<true><<<b->grid, kBT, smem, st>>>(A);
@@ -835,6 +839,22 @@ void batch_info(const BatchImpl* b, long long* info) {
     info[7] = b->nc;
     info[8] = kBT;
     info[9] = 1;
+}
+
+// Test of the bounded waits: with dep_bias = 1 every chain wait asks for one
+// more finished phase than will ever finish, so the first wait runs out after
+// spin_limit sleeps and the call reports HVP_ETIMEOUT. The captured graphs
+// hold the old values and are dropped.
+int batch_wait_test(BatchImpl* b, int dep_bias, long long spin_limit) {
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto& g : b->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    b->dep_bias = dep_bias;
+    b->spin_limit = spin_limit;
+    return HVP_OK;
 }
 
 void batch_free(BatchImpl* b) {

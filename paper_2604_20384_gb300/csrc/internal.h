@@ -166,6 +166,7 @@ int batch_call(BatchImpl* b, const double* G, const double* V, bool dev, double*
 int batch_get(BatchImpl* b, int what, double* out, std::string& err);
 void batch_info(const BatchImpl* b, long long* info);
 void batch_free(BatchImpl* b);
+int batch_wait_test(BatchImpl* b, int dep_bias, long long spin_limit);
 }  // namespace hvp
 
 // Copies a context's reference states (FP32, layout of its last pass) to dst.

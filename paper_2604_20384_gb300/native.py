@@ -53,6 +53,8 @@ def load() -> ctypes.CDLL:
                           "`python -c 'import __graft_entry__ as g; g.build()'`")
     lib = ctypes.CDLL(LIB_PATH)
     vp = ctypes.c_void_p
+    lib.hvp_batch_wait_test.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+    lib.hvp_batch_wait_test.restype = ctypes.c_int
     lib.hvp_num_gates.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.hvp_num_gates.restype = ctypes.c_int
     lib.hvp_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HVPConfig), _dp, _dp]
@@ -283,6 +285,10 @@ class BatchContext(Context):
         self.K = sum(self.Ks)
         self.n_samples = sum(self.ns)
         self.n_circuits = nc
+
+    def wait_test(self, dep_bias: int, spin_limit: int = 20000000):
+        """hvp_batch_wait_test: dep_bias=1 makes the next calls' chain waits run out."""
+        self._check(self._lib.hvp_batch_wait_test(self._h, dep_bias, spin_limit))
 
     def _split(self, flat):
         out, o = [], 0

@@ -58,6 +58,24 @@ def test_batch_window_widths_and_autotune(window, autotune):
         assert rel(hvps[i], o["hvp"]) < TOL, (i, rel(hvps[i], o["hvp"]))
 
 
+def test_expired_chain_wait_is_reported_and_context_stays_usable():
+    # every chain wait asks for a phase that never finishes: the first wait
+    # gives up after 10^4 sleeps of 200 ns, the call reports HVP_ETIMEOUT, and
+    # after restoring the normal waits the same context evaluates correctly
+    ws, circuits = _small_batch()
+    with native.BatchContext(circuits) as b:
+        b.wait_test(1, 10000)
+        with pytest.raises(native.HVPError) as e:
+            b.hvp([w.G for w in ws], [w.V for w in ws])
+        assert e.value.code == native.HVP_ETIMEOUT
+        b.wait_test(0)
+        loss, grads, hvps = b.hvp([w.G for w in ws], [w.V for w in ws])
+    for i, w in enumerate(ws):
+        phi = oracle.reference_states(w.n, w.n_layers, w.Uref, w.psi1q)
+        o = oracle.evaluate(w.n, w.n_layers, w.G, w.V, w.psi1q, phi)
+        assert rel(hvps[i], o["hvp"]) < TOL, (i, rel(hvps[i], o["hvp"]))
+
+
 def test_full_uneven_batch_matches_single_contexts():
     # 64 circuits, n ~ U{8..16}, L ~ U{4..20}, N_s log-uniform in [32, 512]
     shapes = uneven_batch_shapes(64, seed=0)
