@@ -45,6 +45,83 @@ static std::vector<int> smem_order(const std::vector<int>& asc) {
     return out;
 }
 
+// Shared-memory bit order chosen per pass for conflict-free tile loads and
+// stores as well as gates. With 16-byte elements and the swizzle swz(),
+// shared-memory index bit 0, 1, 2 moves an element across 16-byte bank
+// groups 1, 2, 4, bits 3 and 4 both across 7, higher bits not at all. A
+// phase of 8 threads touches 8 elements that differ in three index bits; they
+// avoid each other's bank groups when those bits' images are linearly
+// independent over GF(2). Gates vary the three lowest index bits outside
+// their own two, which are independent as long as no gate has both qubits
+// among bits 0..2 (the triple there is pairwise non-adjacent). Tile loads and
+// stores visit elements in global order, so their phases vary three of the
+// six lowest global address bits of the window (the thread order inside a
+// 64-element block is chosen later, in choose_io_order). This picks the triple
+// for bits 0..2 and the two qubits for bits 3, 4 so that some three of those
+// six global bits have independent images both in the input and in the
+// output layout of the pass; ties keep the fixed order.
+static int gf2_rank3(int a, int b, int c) {
+    int v[3] = {a, b, c}, r = 0;
+    for (int bit = 2; bit >= 0; --bit) {
+        int piv = -1;
+        for (int i = r; i < 3; ++i)
+            if ((v[i] >> bit) & 1) { piv = i; break; }
+        if (piv < 0) continue;
+        std::swap(v[r], v[piv]);
+        for (int i = 0; i < 3; ++i)
+            if (i != r && ((v[i] >> bit) & 1)) v[i] ^= v[r];
+        ++r;
+    }
+    return r;
+}
+
+static std::vector<int> io_aware_smem_order(const std::vector<int>& wq, const std::vector<int>& pos_in,
+                                            const std::vector<int>& pos_out) {
+    const std::vector<int> dflt = smem_order(wq);
+    const int w = (int)wq.size();
+    if (w < 6) return dflt;
+    std::vector<int> B;
+    for (int q : wq) B.push_back(pos_in[q]);
+    std::sort(B.begin(), B.end());
+    int qin[6], qout[6];
+    for (int b = 0; b < 6; ++b)
+        for (int q : wq) {
+            if (pos_in[q] == B[b]) qin[b] = q;
+            if (pos_out[q] == B[b]) qout[b] = q;
+        }
+    auto cost_of = [&](const std::vector<int>& S) {
+        auto img = [&](int q) {
+            for (int i = 0; i < 5; ++i)
+                if (S[i] == q) return i < 3 ? 1 << i : 7;
+            return 0;
+        };
+        int best = 1 << 30;
+        for (int e0 = 0; e0 < 6; ++e0)
+            for (int e1 = e0 + 1; e1 < 6; ++e1)
+                for (int e2 = e1 + 1; e2 < 6; ++e2) {
+                    const int ri = gf2_rank3(img(qin[e0]), img(qin[e1]), img(qin[e2]));
+                    const int ro = gf2_rank3(img(qout[e0]), img(qout[e1]), img(qout[e2]));
+                    best = std::min(best, (1 << (3 - ri)) + (1 << (3 - ro)));
+                }
+        return best;
+    };
+    std::vector<int> best = dflt;
+    int best_cost = cost_of(dflt);
+    for (int a = 0; a < w && best_cost > 2; ++a)
+        for (int b = a + 2; b < w; ++b)
+            for (int c = b + 2; c < w; ++c)
+                for (int x = 0; x < w; ++x)
+                    for (int y = x + 1; y < w; ++y) {
+                        if (x == a || x == b || x == c || y == a || y == b || y == c) continue;
+                        std::vector<int> S = {wq[a], wq[b], wq[c], wq[x], wq[y]};
+                        for (int q : wq)
+                            if (std::find(S.begin(), S.end(), q) == S.end()) S.push_back(q);
+                        const int cst = cost_of(S);
+                        if (cst < best_cost) { best_cost = cst; best = S; }
+                    }
+    return best;
+}
+
 struct Window { int lo, hi; };  // qubits [lo, hi]
 
 static bool in_window(const Window& w, int q) { return q >= w.lo && q <= w.hi; }
@@ -295,6 +372,7 @@ int make_plan(int n, int L, int w, int b, Plan& plan) {
             for (size_t t = 0; t < order.size(); ++t) pos[order[t]] = B[t];
         }
         pp.pos_out = pos;
+        pp.S = io_aware_smem_order(wq, pp.pos_in, pp.pos_out);
         plan.passes.push_back(std::move(pp));
     }
     // Every pass must keep address bits [0, b) local (checked, not assumed).
@@ -306,6 +384,65 @@ int make_plan(int n, int L, int w, int b, Plan& plan) {
         }
     }
     return HVP_OK;
+}
+
+// Shared-memory wavefronts of one tile's load (SMEM slots from the lo/hi
+// tables `slo`, `shi`) when thread t handles tile element perm(t mod 64) +
+// 64 (t / 64): 16-byte accesses are served in phases of 8 lanes, and a phase
+// takes as many wavefronts as the largest number of its lanes that fall in
+// the same 16-byte bank group.
+static long tile_io_wavefronts(const uint16_t* slo, const uint16_t* shi, int w, const int* perm) {
+    const int Lt = 1 << w;
+    long total = 0;
+    for (int base = 0; base < Lt; base += 8) {
+        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 8; ++i) {
+            const int t = base + i;
+            const int m = perm[t & 63] | (t & ~63);
+            const unsigned l = slo[m & 63] | shi[m >> 6];
+            ++cnt[swz(l) & 7];
+        }
+        total += *std::max_element(cnt, cnt + 8);
+    }
+    return total;
+}
+
+// Per pass, the order in which the threads of a CTA visit the elements of a
+// 64-element block during tile loads and stores: the permutation of the six
+// low element-index bits that minimises the shared-memory wavefronts of the
+// load (input layout) plus the store (output layout). Element pairs stay in
+// one 32-byte global sector (index bit 0 comes from a lane bit), so global
+// accesses remain fully used sectors.
+static void choose_io_order(DevPass& d, int w) {
+    if (w < 6) return;
+    int bits[6] = {0, 1, 2, 3, 4, 5};
+    int best_perm[64];
+    long best = -1;
+    do {
+        if (bits[0] == 5) continue;                      // bit 0 of the element index from a lane bit
+        int perm[64];
+        for (int x = 0; x < 64; ++x) {
+            int m = 0;
+            for (int b = 0; b < 6; ++b)
+                if ((x >> bits[b]) & 1) m |= 1 << b;     // element bit b <- thread bit bits[b]
+            perm[x] = m;
+        }
+        const long c = tile_io_wavefronts(d.in_lo, d.in_hi, w, perm) + tile_io_wavefronts(d.out_lo, d.out_hi, w, perm);
+        if (best < 0 || c < best) {
+            best = c;
+            std::copy(perm, perm + 64, best_perm);
+        }
+    } while (std::next_permutation(bits, bits + 6));
+    uint32_t off[64];
+    uint16_t li[64], lo[64];
+    for (int x = 0; x < 64; ++x) {
+        off[x] = d.off_lo[best_perm[x]];
+        li[x] = d.in_lo[best_perm[x]];
+        lo[x] = d.out_lo[best_perm[x]];
+    }
+    std::copy(off, off + 64, d.off_lo);
+    std::copy(li, li + 64, d.in_lo);
+    std::copy(lo, lo + 64, d.out_lo);
 }
 
 void build_dev_passes(const Plan& plan, std::vector<DevPass>& dps, std::vector<DevGate>& dgs) {
@@ -350,6 +487,7 @@ void build_dev_passes(const Plan& plan, std::vector<DevPass>& dps, std::vector<D
                 }
             d.off_hi[y] = off; d.in_hi[y] = (uint16_t)li; d.out_hi[y] = (uint16_t)lo;
         }
+        choose_io_order(d, w);
         for (int g : pp.gates) {
             DevGate dg{};
             dg.k = g;
