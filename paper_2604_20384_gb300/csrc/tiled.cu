@@ -40,7 +40,7 @@ namespace hvp {
 using namespace tile;
 
 // ------------------------------------------------------------ forward kernel
-template <bool TAN, bool P2, int NT>
+template <bool TAN, bool P2, int NT, int GPT = 0>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
     using MT = typename Math<P2>::M;
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledA
         __syncthreads();
         for (int g = 0; g < ngates; ++g) {
             const DevGate dg = a.gates[goff + g];
-            fwd_gate<TAN, P2, NT>(sf, mats + (g * kFwdMats) * 16, mats + (g * kFwdMats + 1) * 16, dg.u, dg.v, Lt);
+            fwd_gate<TAN, P2, NT, const MT*, GPT>(sf, mats + (g * kFwdMats) * 16, mats + (g * kFwdMats + 1) * 16, dg.u,
+                                                   dg.v, Lt);
             __syncthreads();
         }
         if (a.mode & M_STORE_F) store_tile<E, NT>(reinterpret_cast<E*>(a.xout), sf, tc, stlo, sthi, Lt);
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledA
 }
 
 // ----------------------------------------------------------- backward kernel
-template <bool TAN, bool P2, int NT, bool G2 = false>
+template <bool TAN, bool P2, int NT, bool G2 = false, int GPT = 0>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 2 : 1) tiled_bwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
     using MT = typename Math<P2>::M;
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 2 : 1) tiled_bwd_kernel(TiledA
         if (mode & M_FWD) {
             for (int g = 0; g < ngates; ++g) {
                 const DevGate dg = a.gates[goff + g];
-                fwd_gate<TAN, P2, NT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 5) * 16, dg.u, dg.v, Lt);
+                fwd_gate<TAN, P2, NT, const MT*, GPT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 5) * 16, dg.u,
+                                                       dg.v, Lt);
                 __syncthreads();
             }
         }
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 2 : 1) tiled_bwd_kernel(TiledA
                 if (((Lt >> 2) % (2 * NT)) == 0) bwd_gate2<TAN, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
                 else bwd_gate<TAN, false, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
             } else {
-                bwd_gate<TAN, P2, NT, NV>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
+                bwd_gate<TAN, P2, NT, NV, const MT*, GPT>(sf, sb, Gi, Gh, Vm, Vh, dg.u, dg.v, Lt, red);
             }
             warp_reduce_scatter<NV>(red, lane);
             float* wr = wred + ((g & 1) * NW + warp) * 64;
@@ -214,6 +216,18 @@ cudaError_t tiled_set_smem_limits() {
     HVP_SET(false, false, 256); HVP_SET(false, false, 512); HVP_SET(false, true, 256); HVP_SET(false, true, 512);
     HVP_SET(true, false, 128); HVP_SET(false, false, 128);
 #undef HVP_SET
+#define HVP_SET4(K, T, N)                                                                                  \
+    if ((e = cudaFuncSetAttribute(K<T, false, N, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                  227 * 1024)) != cudaSuccess)                                             \
+        return e
+    HVP_SET4(tiled_bwd_kernel, true, 256); HVP_SET4(tiled_bwd_kernel, false, 256);
+#undef HVP_SET4
+#define HVP_SET4(T, N)                                                                                     \
+    if ((e = cudaFuncSetAttribute(tiled_fwd_kernel<T, false, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  227 * 1024)) != cudaSuccess)                                             \
+        return e
+    HVP_SET4(true, 256); HVP_SET4(false, 256);
+#undef HVP_SET4
     return cudaSuccess;
 }
 
@@ -237,7 +251,20 @@ cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, i
     }
     if (threads != 128 && threads != 256 && threads != 512) return cudaErrorInvalidValue;
     if (threads == 128 && variant != 1) return cudaErrorInvalidValue;
-    if (bwd && variant == 3) {
+    // Four groups per thread at 256 threads (12-qubit tiles): kernels with the
+    // group loop unrolled at compile time (3.5-4 % faster on GB300; the same
+    // unrolling at 128 threads with 11-qubit tiles measured 2 % slower, so
+    // that configuration keeps the loop).
+    const bool gpt4 = variant == 1 && threads == 256 && ((1 << w) >> 2) == 4 * threads;
+    if (gpt4) {
+        if (bwd) {
+            if (tangent) tiled_bwd_kernel<true, false, 256, false, 4><<<grid, 256, smem, st>>>(a);
+            else tiled_bwd_kernel<false, false, 256, false, 4><<<grid, 256, smem, st>>>(a);
+        } else {
+            if (tangent) tiled_fwd_kernel<true, false, 256, 4><<<grid, 256, smem, st>>>(a);
+            else tiled_fwd_kernel<false, false, 256, 4><<<grid, 256, smem, st>>>(a);
+        }
+    } else if (bwd && variant == 3) {
         if (tangent) {
             if (threads == 512) tiled_bwd_kernel<true, false, 512, true><<<grid, 512, smem, st>>>(a);
             else tiled_bwd_kernel<true, false, 256, true><<<grid, 256, smem, st>>>(a);

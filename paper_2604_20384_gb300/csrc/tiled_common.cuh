@@ -197,7 +197,15 @@ __device__ __forceinline__ void stage_mats(typename Math<P2>::M* __restrict__ ds
 // One forward gate over all groups of the tile.
 // MA: matrix accessor (a pointer into shared memory, or any type with
 // operator[] returning a matrix element).
-template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*>
+// Number of groups a thread handles in one gate: GPT when it is fixed at
+// compile time (the loop then unrolls), else from the tile size.
+template <int NT, int GPT>
+__device__ __forceinline__ int groups_of_thread(int Lt) {
+    if constexpr (GPT > 0) return GPT;
+    return ((Lt >> 2) + NT - 1 - (int)threadIdx.x) / NT;
+}
+
+template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*, int GPT = 0>
 __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, MA Gm_s, MA Vm_s, int u, int v,
                                          int Lt) {
     const int plo = min(u, v), phi_ = max(u, v);
@@ -211,7 +219,10 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
         Gm[e] = Gm_s[e];
         if constexpr (TAN) Vm[e] = Vm_s[e];
     }
-    for (int q = threadIdx.x; q < (Lt >> 2); q += NT) {
+    const int ng = groups_of_thread<NT, GPT>(Lt);
+#pragma unroll
+    for (int it = 0; it < ng; ++it) {
+        const int q = (int)threadIdx.x + it * NT;
         const unsigned l0 = insert0(insert0(q, plo), phi_);
         const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
         if constexpr (TAN) {
@@ -245,13 +256,16 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
 // before the gate (Vm holds Y = G^-1 V G^-1), add the gate's environment sums
 // to red[] (E then DE, real and imaginary parts interleaved), update the
 // co-states.
-template <bool TAN, bool P2, int NT, int NV, class MA = const typename Math<P2>::M*>
+template <bool TAN, bool P2, int NT, int NV, class MA = const typename Math<P2>::M*, int GPT = 0>
 __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, typename Elt<TAN>::T* __restrict__ sb,
                                          MA Gi, MA Gh, MA Vm, MA Vh, int u, int v, int Lt, float (&red)[NV]) {
     const int tid = threadIdx.x;
     const int plo = min(u, v), phi_ = max(u, v);
     const unsigned mu = 1u << u, mv = 1u << v;
-    for (int q = tid; q < (Lt >> 2); q += NT) {
+    const int ng = groups_of_thread<NT, GPT>(Lt);
+#pragma unroll
+    for (int it = 0; it < ng; ++it) {
+        const int q = tid + it * NT;
         const unsigned l0 = insert0(insert0(q, plo), phi_);
         const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
         if constexpr (TAN) {
