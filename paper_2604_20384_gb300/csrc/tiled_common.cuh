@@ -205,6 +205,38 @@ __device__ __forceinline__ int groups_of_thread(int Lt) {
     return ((Lt >> 2) + NT - 1 - (int)threadIdx.x) / NT;
 }
 
+// Shared-memory slots of the four amplitudes of a thread's it-th group of a
+// gate on index bits u, v (plo < phi_): group q = tid + it * NT spreads over
+// the index bits other than plo and phi_. With GPT fixed, q's bits above
+// log2(NT) come from `it` alone and land on index bits >= 8 (NT = 256), which
+// the swizzle does not touch, so the slots are those of group tid OR-ed with
+// a per-iteration constant.
+template <int NT, int GPT>
+struct GroupIndex {
+    unsigned base[4];
+    unsigned d[GPT > 0 ? GPT : 1];
+    int tid, plo, phi_;
+    unsigned mu, mv;
+    __device__ __forceinline__ GroupIndex(int t, int lo, int hi, unsigned u, unsigned v)
+        : tid(t), plo(lo), phi_(hi), mu(u), mv(v) {
+        if constexpr (GPT > 0) {
+            const unsigned l0 = insert0(insert0(t, lo), hi);
+            base[0] = swz(l0); base[1] = swz(l0 | v); base[2] = swz(l0 | u); base[3] = swz(l0 | u | v);
+#pragma unroll
+            for (int k = 0; k < GPT; ++k) d[k] = insert0(insert0(k * NT, lo), hi);
+        }
+    }
+    __device__ __forceinline__ void get(int it, unsigned (&idx)[4]) const {
+        if constexpr (GPT > 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) idx[c] = base[c] | d[it];
+        } else {
+            const unsigned l0 = insert0(insert0(tid + it * NT, plo), phi_);
+            idx[0] = swz(l0); idx[1] = swz(l0 | mv); idx[2] = swz(l0 | mu); idx[3] = swz(l0 | mu | mv);
+        }
+    }
+};
+
 template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*, int GPT = 0>
 __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, MA Gm_s, MA Vm_s, int u, int v,
                                          int Lt) {
@@ -220,11 +252,11 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
         if constexpr (TAN) Vm[e] = Vm_s[e];
     }
     const int ng = groups_of_thread<NT, GPT>(Lt);
+    GroupIndex<NT, GPT> gi(threadIdx.x, plo, phi_, mu, mv);
 #pragma unroll
     for (int it = 0; it < ng; ++it) {
-        const int q = (int)threadIdx.x + it * NT;
-        const unsigned l0 = insert0(insert0(q, plo), phi_);
-        const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
+        unsigned idx[4];
+        gi.get(it, idx);
         if constexpr (TAN) {
             float2 p[4], d[4], ps[4], ds[4], np[4], nd[4];
 #pragma unroll
@@ -263,11 +295,11 @@ __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
     const int plo = min(u, v), phi_ = max(u, v);
     const unsigned mu = 1u << u, mv = 1u << v;
     const int ng = groups_of_thread<NT, GPT>(Lt);
+    GroupIndex<NT, GPT> gi(tid, plo, phi_, mu, mv);
 #pragma unroll
     for (int it = 0; it < ng; ++it) {
-        const int q = tid + it * NT;
-        const unsigned l0 = insert0(insert0(q, plo), phi_);
-        const unsigned idx[4] = {swz(l0), swz(l0 | mv), swz(l0 | mu), swz(l0 | mu | mv)};
+        unsigned idx[4];
+        gi.get(it, idx);
         if constexpr (TAN) {
             float2 p[4], d[4], A[4], B[4], xs[4], pp[4], pps[4], tt[4], dp[4], dps[4], nA[4], nB[4];
 #pragma unroll
