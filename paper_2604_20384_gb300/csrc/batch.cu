@@ -121,7 +121,11 @@ __device__ __forceinline__ void fwd_gates(typename Elt<TAN>::T* sf, const typena
                                           const BatchArgs& A, const DevPass* P, int nmat, int Lt) {
     for (int g = 0; g < P->n_gates; ++g) {
         const DevGate dg = A.gates[P->gate_off + g];
-        fwd_gate<TAN, false, kBT>(sf, mats + (g * nmat + 4) * 16, mats + (g * nmat + 5) * 16, dg.u, dg.v, Lt);
+        const auto* Gm = mats + (g * nmat + 4) * 16;
+        const auto* Vm = mats + (g * nmat + 5) * 16;
+        // 4096-amplitude tiles: four groups per thread, loop unrolled
+        if (Lt == 4 * 4 * kBT) fwd_gate<TAN, false, kBT, const typename Math<false>::M*, 4>(sf, Gm, Vm, dg.u, dg.v, Lt);
+        else fwd_gate<TAN, false, kBT>(sf, Gm, Vm, dg.u, dg.v, Lt);
         __syncthreads();
     }
 }
@@ -139,7 +143,10 @@ __device__ __forceinline__ void bwd_gates(typename Elt<TAN>::T* sf, typename Elt
         float red[NV];
 #pragma unroll
         for (int e = 0; e < NV; ++e) red[e] = 0.f;
-        bwd_gate<TAN, false, kBT, NV>(sf, sb, base, base + 16, base + 32, base + 48, dg.u, dg.v, Lt, red);
+        if (Lt == 4 * 4 * kBT)
+            bwd_gate<TAN, false, kBT, NV, const typename Math<false>::M*, 4>(sf, sb, base, base + 16, base + 32,
+                                                                            base + 48, dg.u, dg.v, Lt, red);
+        else bwd_gate<TAN, false, kBT, NV>(sf, sb, base, base + 16, base + 32, base + 48, dg.u, dg.v, Lt, red);
         warp_reduce_scatter<NV>(red, lane);
         float* wr = wred + ((g & 1) * NW + warp) * 64;
 #pragma unroll
