@@ -57,7 +57,7 @@ def recorded_traffic(info):
         return None
     for rec in doc.get("records", []):
         plan = rec.get("plan", {})
-        if all(plan.get(k) == info[k] for k in ("window", "threads", "variant", "passes")):
+        if all(plan.get(k) == info[k] for k in ("window", "threads", "variant", "passes", "checkpoint_stride")):
             return rec.get("bwd_kernel_bytes_per_launch")
     return None
 
@@ -189,6 +189,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
     ap.add_argument("--variant", type=int, default=0, help="1 scalar FMA, 2 packed FMA (0 = library default)")
     ap.add_argument("--window", type=int, default=0, help="window qubits (0 = library default)")
+    ap.add_argument("--recompute", action="store_true",
+                    help="recompute forward states inside window passes instead of caching every gate's")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library defaults (or --threads/--variant/--window) instead of autotuning at set-up")
     ap.add_argument("--quick", action="store_true",
@@ -224,7 +226,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
                          stream=stream.cuda_stream, threads=args.threads, variant=args.variant,
-                         window=args.window, autotune=autotune)
+                         window=args.window, autotune=autotune, recompute=args.recompute)
     K = w.K
     G_dev = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
     V_dev = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
@@ -309,9 +311,12 @@ def main():
                                         flops=float(prof["flops"][sel].sum()),
                                         bytes=float(prof["bytes"][sel].sum()))
     total_ms = float(prof["ms"].sum())
-    # Dominant kernel: the backward window-pass kernel (backward passes and the
-    # turnaround pass). Its arithmetic is FP32 SIMT, so the roofline is the FP32
-    # lane rate at the maximum SM clock.
+    # Dominant kernel: the backward window-pass kernel (backward passes and,
+    # when forward states are recomputed, the turnaround pass). Its arithmetic
+    # is FP32 SIMT, so the roofline is the FP32 lane rate at the maximum SM
+    # clock; with the forward cache it also streams 16 B per amplitude per gate
+    # from HBM (the HBM fraction is reported beside it).
+    cached = info["checkpoint_stride"] == 0
     bwd_kinds = [k for k in ("pass_bwd", "pass_turnaround") if k in by_kind]
     p_ms = sum(by_kind[k]["ms"] for k in bwd_kinds)
     p_fl = sum(by_kind[k]["flops"] for k in bwd_kinds)
@@ -326,9 +331,11 @@ def main():
     all_fl = sum(by_kind[k]["flops"] for k in by_kind if k.startswith("pass_"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": recorded_traffic(info),
-                "kernel": f"tiled_bwd_kernel<tangent, {'packed' if info['variant'] == 2 else 'scalar'}, "
-                          f"{info['threads']} threads> (backward and turnaround window passes, "
-                          f"window {info['window']})",
+                "kernel": (f"tiled_bwdc_kernel<tangent, {info['threads']} threads> (backward window passes "
+                           f"reading the forward cache, window {info['window']})" if cached else
+                           f"tiled_bwd_kernel<tangent, {'packed' if info['variant'] == 2 else 'scalar'}, "
+                           f"{info['threads']} threads> (backward and turnaround window passes, "
+                           f"window {info['window']})"),
                 "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
                 "algorithmic_bytes_per_launch": p_by / p_n,
                 "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
@@ -350,6 +357,9 @@ def main():
                        "window": info["window"], "passes": info["passes"], "threads": info["threads"],
                        "variant": info["variant"], "autotuned": autotune,
                        "checkpoint_stride": info["checkpoint_stride"], "tiles_per_cta": info["tiles_per_cta"],
+                       "schedule": ("forward states of every gate cached (Alg. 1), read back by bulk copies"
+                                    if cached else "forward states recomputed inside each window pass"),
+                       "device_mib": info["device_mib"],
                        "l2": "inputs larger than L2 (512 MiB per state set, 129 MB L2)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": info["launches_per_hvp"] * args.steps,

@@ -66,6 +66,10 @@ extern "C" {
 #define HVP_FROBENIUS 32  /* loss, gradient and HVP of the sampled Frobenius
                              cost C_F = 1 - (1/N_s) sum_s Re T_s (Eq. Frobenius,
                              Eq. grad-costF, Eq. hvp-costF) instead of C      */
+#define HVP_RECOMPUTE 64  /* recompute the forward states inside each window
+                             pass with G^-1 instead of keeping the states
+                             before every gate in device memory (see
+                             checkpoint_stride below)                         */
 
 typedef struct hvp_ctx hvp_ctx;
 
@@ -75,8 +79,15 @@ typedef struct {
     int n_samples;         /* N_s >= 1                                         */
     int precision;         /* HVP_C64 or HVP_C128                              */
     int flags;             /* HVP_* flags, or-ed                               */
-    int checkpoint_stride; /* forward checkpoints every this many window
-                              passes, the others recomputed; 0 = automatic     */
+    int checkpoint_stride; /* 0 = automatic: the forward states before every
+                              gate are cached, as in Alg. 1, when K state sets
+                              (16 * 2^n * N_s bytes each) fit in 85 % of the
+                              free device memory and HVP_RECOMPUTE is not set;
+                              otherwise forward checkpoints are kept at window-
+                              pass boundaries (every pass if memory allows) and
+                              the states inside a pass are recomputed with
+                              G^-1. c > 0: checkpoints every c passes, the
+                              others recomputed (no cache)                     */
     int window;            /* local qubits per shared-memory tile; 0 = auto    */
     int threads;           /* threads per CTA of the window-pass kernels,
                               128 (scalar arithmetic, two CTAs per SM when
@@ -178,7 +189,8 @@ int hvp_get(hvp_ctx *ctx, int what, double *out);
 
 /* Description of the execution plan of a context (host memory):
  *   info[0] = K, info[1] = number of window passes P, info[2] = window
- *   (local qubits per tile), info[3] = checkpoint stride, info[4] = kernel
+ *   (local qubits per tile), info[3] = checkpoint stride (0: the forward
+ *   states before every gate are cached), info[4] = kernel
  *   launches of the last hvp call, info[5] = device memory held by the
  *   context in MiB, info[6] = tiles per CTA, info[7] = CTAs per sample,
  *   info[8] = threads per CTA, info[9] = arithmetic variant. */

@@ -11,6 +11,14 @@
 // With a checkpoint stride c > 1 only every c-th boundary is kept and the
 // others are recomputed segment by segment before the backward passes need
 // them.
+//
+// Forward-cache schedule (the default when it fits in device memory; Alg. 1
+// keeps the forward states of every gate): forward passes 0 .. P-1 also write
+// the states before each of their gates into the cache, then backward passes
+// P-1 .. 0 read them back (bulk copies into shared memory) instead of
+// recomputing them with G^-1 inside each pass. The forward states of the pass
+// boundaries are then only needed by the next forward pass (one buffer,
+// updated in place).
 #include <algorithm>
 #include <array>
 #include <chrono>
@@ -66,6 +74,10 @@ struct hvp_ctx {
     std::vector<void*> slots;  // recomputed boundaries of one segment
     void* d_scratch = nullptr; // non-stored boundaries of the first forward sweep
     void* d_co = nullptr;      // co-states (a, b)
+    bool cache = false;        // forward-cache schedule
+    void* d_cache = nullptr;   // K slots of forward states (states before each gate)
+    size_t cache_slot = 0;     // bytes of one slot (tangent elements)
+    void* d_chain = nullptr;   // forward states between passes (cache schedule)
     void* d_x = nullptr;       // unfused forward states
     double* d_partial = nullptr;
     double* d_env = nullptr;
@@ -156,8 +168,10 @@ const void* boundary_in(hvp_ctx* c, int j) {   // forward states after pass j-1
     return c->d_scratch;
 }
 
+// cached: a pass of the forward-cache schedule (forward passes write the
+// cache, backward passes read it).
 int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool tan, int ld_out, int st_out,
-               const void* mats, const void* phi) {
+               const void* mats, const void* phi, bool cached = false) {
     TiledArgs a{};
     a.pass = c->d_pass + p;
     a.gates = c->d_gates;
@@ -169,6 +183,9 @@ int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool ta
     a.cin = c->d_co;
     a.cout = c->d_co;
     a.partial = c->d_partial;
+    a.cache = c->d_cache;
+    a.cache_slot_bytes = ((size_t)1 << c->cfg.n) * c->cfg.n_samples * (tan ? 16 : 8);
+    a.status = c->d_status;
     a.n = c->cfg.n;
     a.n_samples = c->cfg.n_samples;
     a.mode = mode;
@@ -177,16 +194,21 @@ int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool ta
     a.ld_out_tab = ld_out;
     a.st_out_tab = st_out;
     const int ng = (int)c->plan.passes[p].gates.size();
-    CUDA_TRY(c, launch_tiled(a, tan, c->w, c->threads, std::max(ng, 1), c->stream, c->variant));
+    if (cached) CUDA_TRY(c, launch_tiled_cached(a, tan, c->w, c->threads, std::max(ng, 1), c->stream));
+    else CUDA_TRY(c, launch_tiled(a, tan, c->w, c->threads, std::max(ng, 1), c->stream, c->variant));
     if (c->prof) {
         // Algorithmic work: 12 (36) complex MACs per amplitude per gate forward
         // (backward) with tangents, 4 (12) without; 8 flops per complex MAC.
+        // From the forward cache the backward gate needs 24 (8): the forward
+        // states are read, not recomputed, and cost 16 (8) bytes per
+        // amplitude per gate, written by the forward pass and read back.
         const double amps = (double)((size_t)1 << c->cfg.n) * c->cfg.n_samples;
         const double elt = tan ? 16.0 : 8.0;
         double fl = 0, by = 0;
         if (mode & M_FWD) fl += amps * ng * (tan ? 96.0 : 32.0);
-        if (mode & M_BWD) fl += amps * ng * (tan ? 288.0 : 96.0);
-        if (!(mode & M_GEN)) by += amps * elt;
+        if (mode & M_BWD) fl += amps * ng * (cached ? (tan ? 192.0 : 64.0) : (tan ? 288.0 : 96.0));
+        if (cached) by += amps * ng * elt;
+        if (!(mode & M_GEN) && !(cached && (mode & M_BWD))) by += amps * elt;
         if (mode & M_STORE_F) by += amps * elt;
         if (mode & M_BWD) by += amps * ((mode & M_LOAD_PHI) ? 8.0 : elt);
         if (mode & M_STORE_B) by += amps * elt;
@@ -196,7 +218,29 @@ int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool ta
     return HVP_OK;
 }
 
+// Forward-cache schedule: P forward passes filling the cache (the boundary
+// states chained in place through d_chain), then P cached backward passes.
+int enqueue_cached(hvp_ctx* c, bool tan, int* launches) {
+    const int P = c->P;
+    int rc, L = 0;
+    for (int p = 0; p < P; ++p) {
+        const int mode = (p == 0 ? M_GEN : 0) | M_FWD | (p + 1 < P ? M_STORE_F : 0);
+        if ((rc = tiled_pass(c, p, mode, p ? c->d_chain : nullptr, c->d_chain, tan, 0, 1, c->d_mats, c->d_phi,
+                             true)))
+            return rc;
+        ++L;
+    }
+    for (int p = P - 1; p >= 0; --p) {
+        const int mode = M_BWD | (p == P - 1 ? M_LOAD_PHI : 0) | (p > 0 ? M_STORE_B : 0);
+        if ((rc = tiled_pass(c, p, mode, nullptr, nullptr, tan, 1, 0, c->d_mats, c->d_phi, true))) return rc;
+        ++L;
+    }
+    *launches = L;
+    return HVP_OK;
+}
+
 int enqueue_tiled(hvp_ctx* c, bool tan, int* launches) {
+    if (c->cache) return enqueue_cached(c, tan, launches);
     const int P = c->P, cs = c->stride;
     int rc, L = 0;
     // First forward sweep.
@@ -376,7 +420,8 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (L < 1) return fail(c, HVP_EINVAL, "n_layers must be >= 1");
     if (ns < 1) return fail(c, HVP_EINVAL, "n_samples must be >= 1");
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
-    if (cfg->flags & ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS))
+    if (cfg->flags &
+        ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS | HVP_RECOMPUTE))
         return fail(c, HVP_EINVAL, "unknown flag bits");
     if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
     if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))
@@ -421,17 +466,25 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         for (int k = 0; k < c->K; ++k)
             for (int d = 0; d < 4; ++d) eye[32 * (size_t)k + 2 * (d * 4 + d)] = 1.0;
         double best = 1e300;
-        // candidates: (window, threads, arithmetic); 128-thread CTAs pair up
-        // on one SM when the window's tiles leave room in shared memory
-        std::vector<std::array<int, 3>> cands;
+        // candidates: (window, threads, arithmetic, recompute); 128-thread
+        // CTAs pair up on one SM when the window's tiles leave room in shared
+        // memory; recompute = 0 is the forward-cache schedule (scalar
+        // arithmetic), which a candidate context takes when the cache fits
+        std::vector<std::array<int, 4>> cands;
+        const bool may_cache = !(cfg->flags & HVP_RECOMPUTE) && cfg->checkpoint_stride == 0;
         for (int wdw : windows) {
-            for (int var : {1, 2, 3}) cands.push_back({wdw, 256, var});
-            if (wdw <= 11) cands.push_back({wdw, 128, 1});
+            for (int var : {1, 2, 3}) cands.push_back({wdw, 256, var, 1});
+            if (wdw <= 11) cands.push_back({wdw, 128, 1, 1});
+            if (may_cache) {
+                cands.push_back({wdw, 256, 1, 0});
+                if (wdw <= 11) cands.push_back({wdw, 128, 1, 0});
+            }
         }
         for (const auto& cand : cands) {
             const int wdw = cand[0], var = cand[2];
             hvp_config sc = *cfg;
             sc.flags &= ~HVP_AUTOTUNE;
+            if (cand[3]) sc.flags |= HVP_RECOMPUTE;
             sc.window = wdw >= n ? 0 : wdw;
             sc.threads = cand[1];
             sc.variant = var;
@@ -449,9 +502,11 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
                 tuned.window = sc.window;
                 tuned.threads = sc.threads;
                 tuned.variant = var;
+                tuned.flags = (cfg->flags & ~HVP_RECOMPUTE) | (sc.flags & HVP_RECOMPUTE);
             }
         }
         cudaGetLastError();
+        c->cfg.flags = (c->cfg.flags & ~HVP_RECOMPUTE) | (tuned.flags & HVP_RECOMPUTE);
     }
 
     // Plan.
@@ -502,12 +557,31 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         CUDA_TRY(c, cudaMemcpy(c->d_pass, dp.data(), sizeof(DevPass) * dp.size(), cudaMemcpyHostToDevice));
         if (!dg.empty())
             CUDA_TRY(c, cudaMemcpy(c->d_gates, dg.data(), sizeof(DevGate) * dg.size(), cudaMemcpyHostToDevice));
-        // Checkpoint stride: every boundary if memory allows, else the smallest
-        // stride that fits in 85% of the free device memory.
         const int P = c->P;
         const size_t sbytes = state_elt(c) * dim * ns;
         size_t free_b = 0, total_b = 0;
         CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
+        // Forward-cache schedule (the states before every gate kept, K slots of
+        // one state set each) when the caller did not ask for recomputation or
+        // for a checkpoint stride, the scalar kernels are selected, the cached
+        // backward pass fits in shared memory and the cache plus the chained
+        // boundary states fit in 85 % of the free device memory.
+        const size_t slot = 16 * dim * ns;
+        const bool cache_fits = !(tuned.flags & HVP_RECOMPUTE) && cfg->checkpoint_stride == 0 && c->variant == 1 &&
+                                (c->threads == 128 || c->threads == 256) &&
+                                tiled_cached_smem_bytes(true, c->w, c->threads, c->max_gates) <= 227 * 1024 &&
+                                (double)slot * c->K + (double)sbytes <= 0.85 * (double)free_b;
+        if (cache_fits) {
+            if ((rc = dalloc(c, &c->d_cache, slot * (size_t)c->K))) return rc;
+            if ((rc = dalloc(c, &c->d_chain, sbytes))) return rc;
+            c->cache = true;
+            c->cache_slot = slot;
+            c->stride = 1;
+            c->s0_last = 0;
+            c->ckpt.assign(P + 1, nullptr);
+        }
+        // Checkpoint stride: every boundary if memory allows, else the smallest
+        // stride that fits in 85% of the free device memory.
         int cs = cfg->checkpoint_stride;
         auto need = [&](int s) {
             const int stored = (P - 1) / s;
@@ -521,18 +595,20 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
             while (cs < std::max(P, 1) && need(cs) > (size_t)(0.85 * (double)free_b)) ++cs;
         }
         cs = std::max(1, std::min(cs, std::max(P, 1)));
-        c->stride = cs;
-        c->s0_last = ((P - 1) / cs) * cs;
-        c->ckpt.assign(P + 1, nullptr);
-        for (int j = 1; j <= P - 1; ++j)
-            if (j % cs == 0)
-                if ((rc = dalloc(c, &c->ckpt[j], sbytes))) return rc;
-        c->n_slots = std::max(cs - 1, P - 1 - c->s0_last);
-        c->slots.assign(c->n_slots, nullptr);
-        for (int i = 0; i < c->n_slots; ++i)
-            if ((rc = dalloc(c, &c->slots[i], sbytes))) return rc;
-        if (cs > 1 && c->s0_last > 1)
-            if ((rc = dalloc(c, &c->d_scratch, sbytes))) return rc;
+        if (!c->cache) {
+            c->stride = cs;
+            c->s0_last = ((P - 1) / cs) * cs;
+            c->ckpt.assign(P + 1, nullptr);
+            for (int j = 1; j <= P - 1; ++j)
+                if (j % cs == 0)
+                    if ((rc = dalloc(c, &c->ckpt[j], sbytes))) return rc;
+            c->n_slots = std::max(cs - 1, P - 1 - c->s0_last);
+            c->slots.assign(c->n_slots, nullptr);
+            for (int i = 0; i < c->n_slots; ++i)
+                if ((rc = dalloc(c, &c->slots[i], sbytes))) return rc;
+            if (cs > 1 && c->s0_last > 1)
+                if ((rc = dalloc(c, &c->d_scratch, sbytes))) return rc;
+        }
     }
 
     // Input states.
@@ -589,6 +665,7 @@ int call_impl(hvp_ctx* c, const double* G, const double* V, double* loss, double
     CUDA_TRY(c, cudaMemcpyAsync(c->h_res, c->d_res, sizeof(double) * c->res_len, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (*c->h_status & 2) return fail(c, HVP_ETIMEOUT, "a bounded wait for a forward-cache copy expired");
     if (*c->h_status) return fail(c, HVP_ENONFINITE, "a gate is singular or not finite");
     const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
     const double* g = c->h_res + (riem ? c->off_gr() : c->off_ge());
@@ -825,7 +902,7 @@ int hvp_plan_info(const hvp_ctx* c, long long info[10]) {
     info[0] = c->K;
     info[1] = c->unfused ? c->K : c->P;
     info[2] = c->w;
-    info[3] = c->stride;
+    info[3] = c->cache ? 0 : c->stride;
     info[4] = c->launches_per_call[1];
     info[5] = (long long)(c->bytes >> 20);
     info[6] = c->tiles_per_cta;

@@ -99,6 +99,10 @@ struct TiledArgs {
     const void* cin;             // co-states in
     void* cout;                  // co-states out
     double* partial;             // [K][N_s][CX][64]
+    void* cache;                 // forward cache: slot k = states before gate k (pass order), per
+                                 // (sample, tile) one block of 2^w elements in shared-memory order
+    size_t cache_slot_bytes;     // bytes of one cache slot (2^n * N_s elements)
+    int* status;                 // bit 2: a bounded wait for a cache copy gave up
     int n, n_samples, mode, tiles_per_cta, cx_count;
     int ld_out_tab;              // 1: load through the output-layout tables
     int st_out_tab;              // 1: store through the output-layout tables
@@ -110,6 +114,12 @@ struct TiledArgs {
 cudaError_t launch_tiled(const TiledArgs& a, bool tangent, int w, int threads, int max_gates,
                          cudaStream_t st, int variant = 1);
 size_t tiled_smem_bytes(bool tangent, int mode, int w, int threads, int max_gates, int variant = 1);
+// Forward-cache schedule: forward passes (mode M_FWD) that also write the
+// states before every gate to a.cache, and backward passes (mode M_BWD) that
+// read them back instead of recomputing them. threads: 128 or 256.
+cudaError_t launch_tiled_cached(const TiledArgs& a, bool tangent, int w, int threads, int max_gates,
+                                cudaStream_t st);
+size_t tiled_cached_smem_bytes(bool tangent, int w, int threads, int max_gates);
 cudaError_t tiled_set_smem_limits();
 
 // Unfused (one launch per gate) kernels, real type R = float or double.

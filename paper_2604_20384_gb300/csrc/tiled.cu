@@ -40,7 +40,7 @@ namespace hvp {
 using namespace tile;
 
 // ------------------------------------------------------------ forward kernel
-template <bool TAN, bool P2, int NT, int GPT = 0>
+template <bool TAN, bool P2, int NT, int GPT = 0, bool DUMP = false>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledArgs a) {
     using E = typename Elt<TAN>::T;
     using MT = typename Math<P2>::M;
@@ -66,10 +66,19 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledA
         if (a.mode & M_GEN) gen_tile<E, NT>(sf, P, a.psi1q + (size_t)s * a.n * 2, t, P->nq, ng, Lt, a.n);
         else load_tile<E, NT>(sf, reinterpret_cast<const E*>(a.xin), tc, ldlo, ldhi, Lt);
         __syncthreads();
+        if (DUMP && ngates > 0) {   // forward cache: the states before the pass's first gate
+            E* d0 = cache_tile<E>(a, goff, s, t, P->ng, Lt);
+            for (int m = threadIdx.x; m < Lt; m += NT) d0[m] = sf[m];
+        }
         for (int g = 0; g < ngates; ++g) {
             const DevGate dg = a.gates[goff + g];
-            fwd_gate<TAN, P2, NT, const MT*, GPT>(sf, mats + (g * kFwdMats) * 16, mats + (g * kFwdMats + 1) * 16, dg.u,
-                                                   dg.v, Lt);
+            const MT* Gm = mats + (g * kFwdMats) * 16;
+            const MT* Vm = mats + (g * kFwdMats + 1) * 16;
+            if (DUMP && g + 1 < ngates)   // and the states after every gate but the last
+                fwd_gate<TAN, P2, NT, const MT*, GPT, true>(sf, Gm, Vm, dg.u, dg.v, Lt,
+                                                            cache_tile<E>(a, goff + g + 1, s, t, P->ng, Lt));
+            else
+                fwd_gate<TAN, P2, NT, const MT*, GPT>(sf, Gm, Vm, dg.u, dg.v, Lt);
             __syncthreads();
         }
         if (a.mode & M_STORE_F) store_tile<E, NT>(reinterpret_cast<E*>(a.xout), sf, tc, stlo, sthi, Lt);
@@ -182,6 +191,179 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 2 : 1) tiled_bwd_kernel(TiledA
     }
 }
 
+// ------------------------------------------- backward kernel, cached states
+// Forward states before every gate are read from the forward cache instead of
+// being recomputed with G^-1: per gate, the tile's cached states (one
+// contiguous 2^w-element block in shared-memory order) arrive by a bulk copy
+// into one of two shared-memory buffers while the previous gate is computed.
+// Thread 0 issues the copies; every thread waits on the copy's mbarrier with
+// a bound. A thread that gives up raises a shared stop flag and bit 2 of
+// *a.status; the flag is read after a barrier, so the CTA leaves its loops
+// together, thread 0 waits (again bounded) for its copies in flight, and the
+// CTA returns without writing environment records.
+constexpr unsigned kCopyWaitLimit = 1u << 23;
+
+template <bool TAN, int NT, int GPT = 0>
+__global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
+    using E = typename Elt<TAN>::T;
+    constexpr int NW = NT / 32;
+    constexpr int NV = TAN ? 64 : 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+
+    const DevPass* __restrict__ P = a.pass;
+    const int w = P->w, ng = P->ng, ngates = P->n_gates, goff = P->gate_off;
+    const int Lt = 1 << w;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = blockIdx.y;
+    const int mode = a.mode;
+    const unsigned bytes = (unsigned)(Lt * sizeof(E));
+
+    E* sb = reinterpret_cast<E*>(smem);
+    E* const buf0 = sb + Lt;       // cache buffers (even and odd steps of the gate loop)
+    E* const buf1 = sb + 2 * Lt;
+    float2* mats = reinterpret_cast<float2*>(sb + 3 * Lt);     // [gate][G^dag, V^dag][16]
+    float* wred = reinterpret_cast<float*>(mats + ngates * 2 * 16);
+    float* acc = wred + 2 * NW * 64;                           // [ngates][NV] FP32 per CTA
+    uint64_t* bars = reinterpret_cast<uint64_t*>(acc + ngates * NV);
+    volatile int* stop = reinterpret_cast<volatile int*>(bars + 2);
+
+    const int which[2] = {2, 4};   // G^dag, V^dag
+    stage_mats<false, NT>(mats, a, goff, ngates, 2, which);
+    for (int i = tid; i < ngates * NV; i += NT) acc[i] = 0.f;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        *stop = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    // Copy bookkeeping, one bit per buffer: parity of the barrier's next phase
+    // (every thread), and whether a copy into the buffer is outstanding
+    // (thread 0, which issues them).
+    unsigned par = 0u, pend = 0u;
+    const size_t sample_off = (size_t)s << a.n;
+    TileCtx tc{0, P->off_lo, P->off_hi};
+    const uint16_t* ldlo = a.ld_out_tab ? P->out_lo : P->in_lo;
+    const uint16_t* ldhi = a.ld_out_tab ? P->out_hi : P->in_hi;
+    const uint16_t* stlo = a.st_out_tab ? P->out_lo : P->in_lo;
+    const uint16_t* sthi = a.st_out_tab ? P->out_hi : P->in_hi;
+
+    for (int it = 0; it < a.tiles_per_cta; ++it) {
+        const unsigned t = blockIdx.x * a.tiles_per_cta + it;
+        tc.base = tile_base(P, t, sample_off, ng);
+        if (tid == 0 && ngates > 0) {   // cached states of the pass's last two gates
+            fence_proxy_async_smem();
+            bulk_load_async(buf0, cache_tile<E>(a, goff + ngates - 1, s, t, ng, Lt), bytes, &bars[0]);
+            pend |= 1u;
+            if (ngates > 1) {
+                bulk_load_async(buf1, cache_tile<E>(a, goff + ngates - 2, s, t, ng, Lt), bytes, &bars[1]);
+                pend |= 2u;
+            }
+        }
+        if (mode & M_LOAD_PHI) {
+            for (int m = tid; m < Lt; m += NT) {
+                const size_t addr = tc.base + __ldg(&tc.offlo[m & 63]) + __ldg(&tc.offhi[m >> 6]);
+                const unsigned l = __ldg(&ldlo[m & 63]) | __ldg(&ldhi[m >> 6]);
+                const float2 ph = a.phi[addr];
+                if constexpr (TAN) sb[swz(l)] = make_float4(ph.x, ph.y, 0.f, 0.f);
+                else sb[swz(l)] = ph;
+            }
+        } else {
+            load_tile<E, NT>(sb, reinterpret_cast<const E*>(a.cin), tc, ldlo, ldhi, Lt);
+        }
+
+        for (int i = 0; i < ngates; ++i) {
+            const int g = ngates - 1 - i, b = i & 1;
+            E* const cur = b ? buf1 : buf0;
+            if (mbar_wait_bounded(&bars[b], (par >> b) & 1u, kCopyWaitLimit)) {
+                par ^= 1u << b;
+                pend &= ~(1u << b);
+            } else {
+                *stop = 1;
+                atomicOr(a.status, 2);
+            }
+            __syncthreads();
+            if (*stop) break;
+            const DevGate dg = a.gates[goff + g];
+            float red[NV];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) red[e] = 0.f;
+            bwd_gate_cached<TAN, NT, NV, GPT>(cur, sb, mats + (g * 2) * 16, mats + (g * 2 + 1) * 16, dg.u, dg.v,
+                                              Lt, red);
+            warp_reduce_scatter<NV>(red, lane);
+            float* wr = wred + ((g & 1) * NW + warp) * 64;
+#pragma unroll
+            for (int k = 0; k < NV / 32; ++k) wr[lane * (NV / 32) + k] = red[k];
+            __syncthreads();
+            if (tid == 0 && i + 2 < ngates) {   // buffer b is free again: cached states two gates ahead
+                fence_proxy_async_smem();
+                bulk_load_async(cur, cache_tile<E>(a, goff + g - 2, s, t, ng, Lt), bytes, &bars[b]);
+                pend |= 1u << b;
+            }
+            if (tid < NV) {
+                float sum = 0.f;
+#pragma unroll
+                for (int ww = 0; ww < NW; ++ww) sum += wred[((g & 1) * NW + ww) * 64 + tid];
+                acc[g * NV + tid] += sum;
+            }
+        }
+        if (*stop) break;
+        if (mode & M_STORE_B) store_tile<E, NT>(reinterpret_cast<E*>(a.cout), sb, tc, stlo, sthi, Lt);
+        __syncthreads();
+    }
+
+    if (*stop) {   // a copy did not arrive: let the ones still in flight land before the CTA ends
+        if (tid == 0)
+            for (int j = 0; j < 2; ++j)
+                if ((pend >> j) & 1u) mbar_wait_bounded(&bars[j], (par >> j) & 1u, kCopyWaitLimit);
+        return;
+    }
+    for (int i = tid; i < ngates * 64; i += NT) {
+        const int g = i >> 6, e = i & 63;
+        const int k = a.gates[goff + g].k;
+        double* dst = a.partial + (((size_t)k * a.n_samples + s) * a.cx_count + blockIdx.x) * 64;
+        dst[e] = e < NV ? (double)acc[g * NV + e] : 0.0;
+    }
+}
+
+size_t tiled_cached_smem_bytes(bool tangent, int w, int threads, int max_gates) {
+    const size_t elt = tangent ? 16 : 8;
+    size_t b = 3 * (elt << w);                                  // co-states + two cache buffers
+    b += (size_t)max_gates * 2 * 16 * 8;                        // G^dag, V^dag
+    b += 2 * (size_t)(threads / 32) * 64 * 4;                   // cross-warp buffer
+    b += (size_t)max_gates * (tangent ? 64 : 32) * 4;           // FP32 sums
+    b += 32;                                                    // mbarriers, stop flag
+    return b;
+}
+
+// Forward pass that also fills the forward cache (states before each gate),
+// and the cached backward pass.
+cudaError_t launch_tiled_cached(const TiledArgs& a, bool tangent, int w, int threads, int n_gates, cudaStream_t st) {
+    const bool bwd = (a.mode & M_BWD) != 0;
+    if ((a.mode & M_FWD) && bwd) return cudaErrorInvalidValue;
+    if (threads != 128 && threads != 256) return cudaErrorInvalidValue;
+    const size_t smem = bwd ? tiled_cached_smem_bytes(tangent, w, threads, n_gates)
+                            : tiled_smem_bytes(tangent, a.mode, w, threads, n_gates, 1);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    dim3 grid(a.cx_count, a.n_samples);
+    const bool gpt4 = threads == 256 && ((1 << w) >> 2) == 4 * threads;
+#define HVP_C(T, N, G)                                                                            \
+    do {                                                                                          \
+        if (bwd) tiled_bwdc_kernel<T, N, G><<<grid, N, smem, st>>>(a);                            \
+        else tiled_fwd_kernel<T, false, N, G, true><<<grid, N, smem, st>>>(a);                    \
+    } while (0)
+    if (gpt4) {
+        if (tangent) HVP_C(true, 256, 4); else HVP_C(false, 256, 4);
+    } else if (threads == 256) {
+        if (tangent) HVP_C(true, 256, 0); else HVP_C(false, 256, 0);
+    } else {
+        if (tangent) HVP_C(true, 128, 0); else HVP_C(false, 128, 0);
+    }
+#undef HVP_C
+    return cudaGetLastError();
+}
+
 size_t tiled_smem_bytes(bool tangent, int mode, int w, int threads, int max_gates, int variant) {
     const bool bwd = (mode & M_BWD) != 0;
     const size_t elt = tangent ? 16 : 8;
@@ -228,6 +410,15 @@ cudaError_t tiled_set_smem_limits() {
         return e
     HVP_SET4(true, 256); HVP_SET4(false, 256);
 #undef HVP_SET4
+#define HVP_SETC(T, N, G)                                                                                  \
+    if ((e = cudaFuncSetAttribute(tiled_bwdc_kernel<T, N, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                  227 * 1024)) != cudaSuccess ||                                           \
+        (e = cudaFuncSetAttribute(tiled_fwd_kernel<T, false, N, G, true>,                                 \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024)) != cudaSuccess) \
+        return e
+    HVP_SETC(true, 256, 4); HVP_SETC(false, 256, 4); HVP_SETC(true, 256, 0); HVP_SETC(false, 256, 0);
+    HVP_SETC(true, 128, 0); HVP_SETC(false, 128, 0);
+#undef HVP_SETC
     return cudaSuccess;
 }
 

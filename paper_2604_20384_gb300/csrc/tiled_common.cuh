@@ -128,6 +128,66 @@ struct TileCtx {
     const uint32_t* offhi;
 };
 
+// ------------------------------------------------- bulk copies and mbarriers
+// One-dimensional bulk copies (cp.async.bulk, the TMA engine without a tensor
+// map) from global into shared memory, completed on an mbarrier by byte
+// count. Sizes and both addresses are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes initialised mbarriers and earlier generic-proxy shared-memory accesses
+// of this thread visible to the async proxy (bulk copies).
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load_async(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits until the barrier's phase with the given parity has completed; gives
+// up (returns false) after `limit` polls, the later ones 256 ns apart
+// (limit = 1 << 23: about two seconds).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i) {
+        if (mbar_test(bar, parity)) return true;
+        if (i >= 64) __nanosleep(256);
+    }
+    return false;
+}
+
+// Tile t of sample s in slot `slot` of the forward cache (slot k: the forward
+// states before gate k in pass order), one contiguous block of 2^w elements
+// in shared-memory order.
+template <typename E>
+__device__ __forceinline__ E* cache_tile(const TiledArgs& a, int slot, int s, unsigned t, int ng, int Lt) {
+    return reinterpret_cast<E*>(static_cast<char*>(a.cache) + (size_t)slot * a.cache_slot_bytes) +
+           (((size_t)s << ng) + t) * (size_t)Lt;
+}
+
 __device__ __forceinline__ size_t tile_base(const DevPass* __restrict__ P, unsigned t, size_t sample_off, int ng) {
     size_t base = sample_off;
     for (int r = 0; r < ng; ++r)
@@ -237,9 +297,11 @@ struct GroupIndex {
     }
 };
 
-template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*, int GPT = 0>
+// With DUMP, the states after the gate are also written to `dump` (global
+// memory, same element order as the shared-memory tile).
+template <bool TAN, bool P2, int NT, class MA = const typename Math<P2>::M*, int GPT = 0, bool DUMP = false>
 __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, MA Gm_s, MA Vm_s, int u, int v,
-                                         int Lt) {
+                                         int Lt, typename Elt<TAN>::T* __restrict__ dump = nullptr) {
     const int plo = min(u, v), phi_ = max(u, v);
     const unsigned mu = 1u << u, mv = 1u << v;
     // The gate's matrices are read from shared memory once per thread and
@@ -270,7 +332,11 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
 #pragma unroll
                 for (int c = 0; c < 4; ++c) Math<P2>::mac(nd[r], Vm[r * 4 + c], p[c], ps[c]);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) sf[idx[r]] = make_float4(np[r].x, np[r].y, nd[r].x, nd[r].y);
+            for (int r = 0; r < 4; ++r) {
+                const float4 o = make_float4(np[r].x, np[r].y, nd[r].x, nd[r].y);
+                sf[idx[r]] = o;
+                if constexpr (DUMP) dump[idx[r]] = o;
+            }
         } else {
             float2 p[4], ps[4], np[4];
 #pragma unroll
@@ -278,7 +344,10 @@ __device__ __forceinline__ void fwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
             swaps<P2>(p, ps);
             matvec4<P2>(Gm, p, ps, np);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) sf[idx[r]] = np[r];
+            for (int r = 0; r < 4; ++r) {
+                sf[idx[r]] = np[r];
+                if constexpr (DUMP) dump[idx[r]] = np[r];
+            }
         }
     }
 }
@@ -370,6 +439,76 @@ __device__ __forceinline__ void bwd_gate(typename Elt<TAN>::T* __restrict__ sf, 
             matvec4<P2>(Gh, A, xs, nA);
 #pragma unroll
             for (int r = 0; r < 4; ++r) { sf[idx[r]] = pp[r]; sb[idx[r]] = nA[r]; }
+        }
+    }
+}
+
+// One backward gate with the forward states before the gate taken from a
+// cache (sc: psi^[k-1], dpsi^[k-1] as written by the forward pass) instead of
+// being recomputed: environment sums with the pre-update co-states, then the
+// co-state update (Eq. environment, Eq. Dpsi, Eq. bis, Eq. dbis).
+template <bool TAN, int NT, int NV, int GPT = 0>
+__device__ __forceinline__ void bwd_gate_cached(const typename Elt<TAN>::T* __restrict__ sc,
+                                                typename Elt<TAN>::T* __restrict__ sb, const float2* Gh,
+                                                const float2* Vh, int u, int v, int Lt, float (&red)[NV]) {
+    using M = Math<false>;
+    const int plo = min(u, v), phi_ = max(u, v);
+    const unsigned mu = 1u << u, mv = 1u << v;
+    const int ng = groups_of_thread<NT, GPT>(Lt);
+    GroupIndex<NT, GPT> gi(threadIdx.x, plo, phi_, mu, mv);
+#pragma unroll
+    for (int it = 0; it < ng; ++it) {
+        unsigned idx[4];
+        gi.get(it, idx);
+        if constexpr (TAN) {
+            float2 pp[4], dp[4], A[4], B[4], nA[4], nB[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float4 x = sc[idx[c]];
+                const float4 y = sb[idx[c]];
+                pp[c] = lo2(x); dp[c] = hi2(x); A[c] = lo2(y); B[c] = hi2(y);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                    M::cmac(e1, A[i], pp[j], pp[j]);
+                    red[2 * (i * 4 + j)] = e1.x;
+                    red[2 * (i * 4 + j) + 1] = e1.y;
+                    float2 e2 = make_float2(red[32 + 2 * (i * 4 + j)], red[32 + 2 * (i * 4 + j) + 1]);
+                    M::cmac(e2, B[i], pp[j], pp[j]);
+                    M::cmac(e2, A[i], dp[j], dp[j]);
+                    red[32 + 2 * (i * 4 + j)] = e2.x;
+                    red[32 + 2 * (i * 4 + j) + 1] = e2.y;
+                }
+            matvec4<false>(Gh, A, A, nA);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                nB[r] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) M::mac(nB[r], Vh[r * 4 + c], A[c], A[c]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) M::mac(nB[r], Gh[r * 4 + c], B[c], B[c]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sb[idx[r]] = make_float4(nA[r].x, nA[r].y, nB[r].x, nB[r].y);
+        } else {
+            float2 pp[4], A[4], nA[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { pp[c] = sc[idx[c]]; A[c] = sb[idx[c]]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float2 e1 = make_float2(red[2 * (i * 4 + j)], red[2 * (i * 4 + j) + 1]);
+                    M::cmac(e1, A[i], pp[j], pp[j]);
+                    red[2 * (i * 4 + j)] = e1.x;
+                    red[2 * (i * 4 + j) + 1] = e1.y;
+                }
+            matvec4<false>(Gh, A, A, nA);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) sb[idx[r]] = nA[r];
         }
     }
 }

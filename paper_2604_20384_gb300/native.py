@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hvp.h")
 HVP_OK, HVP_EINVAL, HVP_ENOMEM, HVP_ECUDA, HVP_ETIMEOUT, HVP_ENONFINITE = 0, -1, -2, -3, -4, -5
 HVP_C64, HVP_C128 = 0, 1
 HVP_RIEMANNIAN, HVP_PHI_GIVEN, HVP_UNFUSED, HVP_NO_GRAPH, HVP_AUTOTUNE, HVP_FROBENIUS = 1, 2, 4, 8, 16, 32
+HVP_RECOMPUTE = 64
 KINDS = {0: "prep", 1: "pass_fwd", 2: "pass_turnaround", 3: "pass_bwd", 4: "gate_init", 5: "gate_fwd",
          6: "gate_load_phi", 7: "gate_bwd", 8: "post"}
 OUT = dict(T=1, Omega=2, grad_e=3, hvp_e=4, grad_r=5, hvp_r=6, loss=7, env=8)
@@ -145,15 +146,16 @@ class Context:
     def __init__(self, n: int, n_layers: int, psi1q, ref, *, precision: str = "c64",
                  riemannian: bool = False, phi_given: bool = False, unfused: bool = False,
                  graphs: bool = True, checkpoint_stride: int = 0, window: int = 0, threads: int = 0,
-                 variant: int = 0, autotune: bool = False, frobenius: bool = False, device: int = 0,
-                 stream: int | None = None):
+                 variant: int = 0, autotune: bool = False, frobenius: bool = False, recompute: bool = False,
+                 device: int = 0, stream: int | None = None):
         self._lib = load()
         psi1q = np.asarray(psi1q)
         self.n, self.n_layers, self.n_samples = n, n_layers, int(psi1q.shape[0])
         self.K = self._lib.hvp_num_gates(n, n_layers)
         flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
                  | (HVP_UNFUSED if unfused else 0) | (0 if graphs else HVP_NO_GRAPH)
-                 | (HVP_AUTOTUNE if autotune else 0) | (HVP_FROBENIUS if frobenius else 0))
+                 | (HVP_AUTOTUNE if autotune else 0) | (HVP_FROBENIUS if frobenius else 0)
+                 | (HVP_RECOMPUTE if recompute else 0))
         cfg = HVPConfig(n, n_layers, self.n_samples, HVP_C128 if precision == "c128" else HVP_C64, flags,
                         checkpoint_stride, window, threads, variant, device, stream)
         self._psi = _f64(psi1q)

@@ -60,25 +60,37 @@ def test_n12_precision_comparison(precision):
         _check(ctx, w, o, TOL[precision])
 
 
+@pytest.mark.parametrize("recompute", [False, True])
 @pytest.mark.parametrize("n,L,ns,window", [(14, 7, 5, 10), (16, 9, 3, 12), (13, 11, 7, 8), (15, 6, 2, 9),
                                            (10, 12, 9, 6)])
-def test_multi_pass_tiles_with_ragged_shapes(n, L, ns, window):
-    # several passes, several tiles per sample, layouts permuted between passes
+def test_multi_pass_tiles_with_ragged_shapes(n, L, ns, window, recompute):
+    # several passes, several tiles per sample, layouts permuted between
+    # passes; both schedules (forward states cached before every gate, or
+    # recomputed inside each pass from boundary checkpoints)
     w = make_workload(n, L, ns, seed=n + L)
     o, phi = _oracle(w)
-    with native.Context(n, L, w.psi1q, w.Uref, window=window) as ctx:
-        assert ctx.plan_info()["passes"] > 1
+    with native.Context(n, L, w.psi1q, w.Uref, window=window, recompute=recompute) as ctx:
+        info = ctx.plan_info()
+        assert info["passes"] > 1
+        assert (info["checkpoint_stride"] == 0) == (not recompute)
         _check(ctx, w, o, TOL["c64"])
 
 
-@pytest.mark.parametrize("threads,variant", [(256, 1), (256, 2), (512, 1), (512, 2), (256, 3), (512, 3), (128, 1)])
-def test_kernel_variants_match_oracle(threads, variant):
-    # every thread count and arithmetic form of the window-pass kernels
+@pytest.mark.parametrize("threads,variant,recompute", [(256, 1, False), (256, 1, True), (256, 2, False),
+                                                       (512, 1, False), (512, 2, False), (256, 3, False),
+                                                       (512, 3, False), (128, 1, False), (128, 1, True)])
+def test_kernel_variants_match_oracle(threads, variant, recompute):
+    # every thread count and arithmetic form of the window-pass kernels (the
+    # forward-cache schedule runs the scalar kernels at 128 and 256 threads;
+    # the other forms recompute)
     w = make_workload(15, 9, 6, seed=44)
     o, phi = _oracle(w)
-    with native.Context(15, 9, w.psi1q, w.Uref, window=11, threads=threads, variant=variant) as ctx:
+    with native.Context(15, 9, w.psi1q, w.Uref, window=11, threads=threads, variant=variant,
+                        recompute=recompute) as ctx:
         info = ctx.plan_info()
         assert info["threads"] == threads and info["variant"] == variant and info["passes"] > 1
+        cached = variant == 1 and threads in (128, 256) and not recompute
+        assert (info["checkpoint_stride"] == 0) == cached
         _check(ctx, w, o, TOL["c64"])
         loss, grad = ctx.loss_grad(w.G)
         assert rel(grad, o["grad"]) < TOL["c64"]
@@ -219,16 +231,20 @@ def test_maximum_size_solution_point_and_directional_derivative():
     assert abs(fd - an) < 1e-3 * an, (fd, an)
 
 
-@pytest.mark.parametrize("threads,window", [(0, 0), (128, 11)])
-def test_headline_shape_sampled_against_oracle(threads, window):
-    # n = 20, L = 16, N_s = 64 in the benchmark's launch configurations (the
-    # library defaults and the autotuner's choice on GB300); the oracle checks
-    # two of the samples one by one (T_s, Omega_s and every per-sample
-    # environment), and the sample-summed outputs are checked through
-    # linearity in the samples.
+@pytest.mark.parametrize("threads,window,recompute", [(0, 0, False), (128, 11, False), (0, 0, True),
+                                                      (128, 11, True)])
+def test_headline_shape_sampled_against_oracle(threads, window, recompute):
+    # n = 20, L = 16, N_s = 64 in the benchmark's launch configurations (12-
+    # and 11-qubit windows; forward states cached before every gate, 152 GiB,
+    # or recomputed inside each pass); the oracle checks two of the samples
+    # one by one (T_s, Omega_s and every per-sample environment), and the
+    # sample-summed outputs are checked through linearity in the samples.
     w = make_workload(20, 16, 64, seed=0)
-    with native.Context(20, 16, w.psi1q, w.Uref, threads=threads, window=window) as ctx:
-        assert ctx.plan_info()["passes"] == (4 if window == 0 else 6)
+    with native.Context(20, 16, w.psi1q, w.Uref, threads=threads, window=window, recompute=recompute) as ctx:
+        info = ctx.plan_info()
+        assert info["passes"] == (4 if window == 0 else 6)
+        assert (info["checkpoint_stride"] == 0) == (not recompute)
+        assert info["tiles_per_cta"] > 1
         loss, grad, hvp = ctx.hvp(w.G, w.V)
         T, Om = ctx.get("T"), ctx.get("Omega")
         E, DE = ctx.get("env")
@@ -246,3 +262,28 @@ def test_headline_shape_sampled_against_oracle(threads, window):
     h = -(2 / 64) * (np.einsum("s,skij->kij", Om, E.conj()) + np.einsum("s,skij->kij", T, DE.conj()))
     assert rel(grad, g) < 1e-9 and rel(hvp, h) < 1e-9
     assert abs(loss - (1 - np.mean(np.abs(T) ** 2))) < 1e-12
+
+
+def test_forward_cache_schedule_against_recompute_and_oracle():
+    # Several tiles per CTA (the copy barriers' phases run on across tiles),
+    # several passes, both the tangent and the loss/gradient-only sweeps: the
+    # cached schedule against the oracle, against the recomputing schedule
+    # (same arithmetic except G^-1 recomputation, so close but not
+    # identical) and against itself on a repeated call (bit-identical).
+    n, L, ns = 14, 8, 128
+    w = make_workload(n, L, ns, seed=140)
+    o, phi = _oracle(w)
+    res = {}
+    for recompute in (False, True):
+        with native.Context(n, L, w.psi1q, w.Uref, window=8, recompute=recompute) as ctx:
+            info = ctx.plan_info()
+            assert info["passes"] > 2 and info["tiles_per_cta"] > 1
+            assert (info["checkpoint_stride"] == 0) == (not recompute)
+            r1 = _check(ctx, w, o, TOL["c64"])
+            r2 = ctx.hvp(w.G, w.V)
+            assert r1[0] == r2[0] and np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+            lg = ctx.loss_grad(w.G)
+            assert abs(lg[0] - o["loss"]) <= TOL["c64"] and rel(lg[1], o["grad"]) < TOL["c64"]
+            res[recompute] = r1
+    assert rel(res[False][1], res[True][1]) < 2 * TOL["c64"]
+    assert rel(res[False][2], res[True][2]) < 2 * TOL["c64"]
