@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) tiled_fwd_kernel(TiledA
         if (DUMP && ngates > 0) {   // forward cache: the states before the pass's first gate
             E* d0 = cache_tile<E>(a, goff, s, t, P->ng, Lt);
             for (int m = threadIdx.x; m < Lt; m += NT) d0[m] = sf[m];
+            __syncthreads();         // the first gate updates the tile in place
         }
         for (int g = 0; g < ngates; ++g) {
             const DevGate dg = a.gates[goff + g];
@@ -226,9 +227,11 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
     float* acc = wred + 2 * NW * 64;                           // [ngates][NV] FP32 per CTA
     uint64_t* bars = reinterpret_cast<uint64_t*>(acc + ngates * NV);
     volatile int* stop = reinterpret_cast<volatile int*>(bars + 2);
+    int2* guv = reinterpret_cast<int2*>(bars + 3);            // [gate] shared-memory bits (u, v)
 
     const int which[2] = {2, 4};   // G^dag, V^dag
     stage_mats<false, NT>(mats, a, goff, ngates, 2, which);
+    for (int i = tid; i < ngates; i += NT) guv[i] = make_int2(a.gates[goff + i].u, a.gates[goff + i].v);
     for (int i = tid; i < ngates * NV; i += NT) acc[i] = 0.f;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
@@ -285,11 +288,11 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
             }
             __syncthreads();
             if (*stop) break;
-            const DevGate dg = a.gates[goff + g];
+            const int2 uv = guv[g];
             float red[NV];
 #pragma unroll
             for (int e = 0; e < NV; ++e) red[e] = 0.f;
-            bwd_gate_cached<TAN, NT, NV, GPT>(cur, sb, mats + (g * 2) * 16, mats + (g * 2 + 1) * 16, dg.u, dg.v,
+            bwd_gate_cached<TAN, NT, NV, GPT>(cur, sb, mats + (g * 2) * 16, mats + (g * 2 + 1) * 16, uv.x, uv.y,
                                               Lt, red);
             warp_reduce_scatter<NV>(red, lane);
             float* wr = wred + ((g & 1) * NW + warp) * 64;
@@ -333,7 +336,7 @@ size_t tiled_cached_smem_bytes(bool tangent, int w, int threads, int max_gates) 
     b += (size_t)max_gates * 2 * 16 * 8;                        // G^dag, V^dag
     b += 2 * (size_t)(threads / 32) * 64 * 4;                   // cross-warp buffer
     b += (size_t)max_gates * (tangent ? 64 : 32) * 4;           // FP32 sums
-    b += 32;                                                    // mbarriers, stop flag
+    b += 32 + (size_t)max_gates * 8;                            // mbarriers, stop flag, gate bits
     return b;
 }
 

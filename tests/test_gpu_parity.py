@@ -245,7 +245,9 @@ def test_headline_shape_sampled_against_oracle(threads, window, recompute):
         assert info["passes"] == (4 if window == 0 else 6)
         assert (info["checkpoint_stride"] == 0) == (not recompute)
         assert info["tiles_per_cta"] > 1
+        r0 = ctx.hvp(w.G, w.V)
         loss, grad, hvp = ctx.hvp(w.G, w.V)
+        assert r0[0] == loss and np.array_equal(r0[1], grad) and np.array_equal(r0[2], hvp)
         T, Om = ctx.get("T"), ctx.get("Omega")
         E, DE = ctx.get("env")
     pick = [0, 37]
@@ -264,18 +266,19 @@ def test_headline_shape_sampled_against_oracle(threads, window, recompute):
     assert abs(loss - (1 - np.mean(np.abs(T) ** 2))) < 1e-12
 
 
-def test_forward_cache_schedule_against_recompute_and_oracle():
+@pytest.mark.parametrize("threads", [256, 128])
+def test_forward_cache_schedule_against_recompute_and_oracle(threads):
     # Several tiles per CTA (the copy barriers' phases run on across tiles),
     # several passes, both the tangent and the loss/gradient-only sweeps: the
     # cached schedule against the oracle, against the recomputing schedule
     # (same arithmetic except G^-1 recomputation, so close but not
     # identical) and against itself on a repeated call (bit-identical).
-    n, L, ns = 14, 8, 128
+    n, L, ns = 14, 8, 256
     w = make_workload(n, L, ns, seed=140)
     o, phi = _oracle(w)
     res = {}
     for recompute in (False, True):
-        with native.Context(n, L, w.psi1q, w.Uref, window=8, recompute=recompute) as ctx:
+        with native.Context(n, L, w.psi1q, w.Uref, window=8, threads=threads, recompute=recompute) as ctx:
             info = ctx.plan_info()
             assert info["passes"] > 2 and info["tiles_per_cta"] > 1
             assert (info["checkpoint_stride"] == 0) == (not recompute)
