@@ -143,6 +143,19 @@ int hvp_init_batch(hvp_ctx **out, int n_circuits, const hvp_config *cfgs,
  * dep_bias is not 0 or 1 or spin_limit < 1. */
 int hvp_batch_wait_test(hvp_ctx *ctx, int dep_bias, long long spin_limit);
 
+/* Test of the bounded waits of the forward-cache schedule (no counterpart in
+ * the paper). The cached backward kernel waits on an mbarrier for each bulk
+ * copy of cached forward states; extra_bytes = 16 makes every such barrier
+ * expect 16 bytes more than its copy delivers, so no wait can complete: each
+ * gives up after spin_limit polls (0 = the default of 2^23, about two
+ * seconds), the kernel stops without writing results, and the next
+ * hvp_loss_grad / hvp_hvp call returns HVP_ETIMEOUT; the context stays
+ * usable. extra_bytes = 0 with spin_limit = 0 restores normal operation.
+ * Applies to the next calls (captured graphs are rebuilt). HVP_EINVAL if the
+ * context does not run the forward cache (hvp_plan_info info[3] != 0) or an
+ * argument is out of range. */
+int hvp_cache_wait_test(hvp_ctx *ctx, int extra_bytes, long long spin_limit);
+
 /* Loss and gradient (Alg. 1 without tangents, Alg. 2 first two steps).
  *   G    : host, K*32 doubles.
  *   loss : host, 1 double (may be NULL).

@@ -78,6 +78,7 @@ struct hvp_ctx {
     void* d_cache = nullptr;   // K slots of forward states (states before each gate)
     size_t cache_slot = 0;     // bytes of one slot (tangent elements)
     void* d_chain = nullptr;   // forward states between passes (cache schedule)
+    unsigned copy_wait_limit = 0, copy_extra_bytes = 0;   // hvp_cache_wait_test
     void* d_x = nullptr;       // unfused forward states
     double* d_partial = nullptr;
     double* d_env = nullptr;
@@ -186,6 +187,8 @@ int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool ta
     a.cache = c->d_cache;
     a.cache_slot_bytes = ((size_t)1 << c->cfg.n) * c->cfg.n_samples * (tan ? 16 : 8);
     a.status = c->d_status;
+    a.copy_wait_limit = c->copy_wait_limit;
+    a.copy_extra_bytes = c->copy_extra_bytes;
     a.n = c->cfg.n;
     a.n_samples = c->cfg.n_samples;
     a.mode = mode;
@@ -918,6 +921,22 @@ int hvp_batch_wait_test(hvp_ctx* c, int dep_bias, long long spin_limit) {
     if (dep_bias < 0 || dep_bias > 1 || spin_limit < 1)
         return fail(c, HVP_EINVAL, "hvp_batch_wait_test: dep_bias must be 0 or 1 and spin_limit >= 1");
     return batch_wait_test(c->batch, dep_bias, spin_limit);
+}
+
+int hvp_cache_wait_test(hvp_ctx* c, int extra_bytes, long long spin_limit) {
+    if (!c) return fail(nullptr, HVP_EINVAL, "hvp_cache_wait_test: ctx is NULL");
+    if (!c->cache) return fail(c, HVP_EINVAL, "hvp_cache_wait_test: the context does not run the forward cache");
+    if ((extra_bytes != 0 && extra_bytes != 16) || spin_limit < 0 || spin_limit > 0x7fffffffll)
+        return fail(c, HVP_EINVAL, "hvp_cache_wait_test: extra_bytes must be 0 or 16, spin_limit in [0, 2^31)");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->copy_extra_bytes = (unsigned)extra_bytes;
+    c->copy_wait_limit = (unsigned)spin_limit;
+    for (auto& g : c->gexec)   // the kernel arguments are baked into the captured graphs
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return HVP_OK;
 }
 
 void hvp_free(hvp_ctx* c) {

@@ -103,6 +103,9 @@ struct TiledArgs {
                                  // (sample, tile) one block of 2^w elements in shared-memory order
     size_t cache_slot_bytes;     // bytes of one cache slot (2^n * N_s elements)
     int* status;                 // bit 2: a bounded wait for a cache copy gave up
+    unsigned copy_wait_limit;    // polls before a cache-copy wait gives up (0: the default)
+    unsigned copy_extra_bytes;   // test of the bounded waits: bytes the copy barriers expect
+                                 // beyond what arrives (0 in normal use)
     int n, n_samples, mode, tiles_per_cta, cx_count;
     int ld_out_tab;              // 1: load through the output-layout tables
     int st_out_tab;              // 1: store through the output-layout tables

@@ -218,6 +218,8 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
     const int s = blockIdx.y;
     const int mode = a.mode;
     const unsigned bytes = (unsigned)(Lt * sizeof(E));
+    const unsigned wait_limit = a.copy_wait_limit ? a.copy_wait_limit : kCopyWaitLimit;
+    const unsigned extra = a.copy_extra_bytes;
 
     E* sb = reinterpret_cast<E*>(smem);
     E* const buf0 = sb + Lt;       // cache buffers (even and odd steps of the gate loop)
@@ -257,10 +259,10 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
         tc.base = tile_base(P, t, sample_off, ng);
         if (tid == 0 && ngates > 0) {   // cached states of the pass's last two gates
             fence_proxy_async_smem();
-            bulk_load_async(buf0, cache_tile<E>(a, goff + ngates - 1, s, t, ng, Lt), bytes, &bars[0]);
+            bulk_load_async(buf0, cache_tile<E>(a, goff + ngates - 1, s, t, ng, Lt), bytes, &bars[0], extra);
             pend |= 1u;
             if (ngates > 1) {
-                bulk_load_async(buf1, cache_tile<E>(a, goff + ngates - 2, s, t, ng, Lt), bytes, &bars[1]);
+                bulk_load_async(buf1, cache_tile<E>(a, goff + ngates - 2, s, t, ng, Lt), bytes, &bars[1], extra);
                 pend |= 2u;
             }
         }
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
         for (int i = 0; i < ngates; ++i) {
             const int g = ngates - 1 - i, b = i & 1;
             E* const cur = b ? buf1 : buf0;
-            if (mbar_wait_bounded(&bars[b], (par >> b) & 1u, kCopyWaitLimit)) {
+            if (mbar_wait_bounded(&bars[b], (par >> b) & 1u, wait_limit)) {
                 par ^= 1u << b;
                 pend &= ~(1u << b);
             } else {
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
             __syncthreads();
             if (tid == 0 && i + 2 < ngates) {   // buffer b is free again: cached states two gates ahead
                 fence_proxy_async_smem();
-                bulk_load_async(cur, cache_tile<E>(a, goff + g - 2, s, t, ng, Lt), bytes, &bars[b]);
+                bulk_load_async(cur, cache_tile<E>(a, goff + g - 2, s, t, ng, Lt), bytes, &bars[b], extra);
                 pend |= 1u << b;
             }
             if (tid < NV) {
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
     if (*stop) {   // a copy did not arrive: let the ones still in flight land before the CTA ends
         if (tid == 0)
             for (int j = 0; j < 2; ++j)
-                if ((pend >> j) & 1u) mbar_wait_bounded(&bars[j], (par >> j) & 1u, kCopyWaitLimit);
+                if ((pend >> j) & 1u) mbar_wait_bounded(&bars[j], (par >> j) & 1u, wait_limit);
         return;
     }
     for (int i = tid; i < ngates * 64; i += NT) {

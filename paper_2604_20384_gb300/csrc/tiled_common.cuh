@@ -149,8 +149,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void bulk_load_async(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+// The barrier is told to expect `bytes + extra` bytes: extra = 0 in normal
+// use; a positive extra keeps the phase from completing (test of the bounded
+// waits).
+__device__ __forceinline__ void bulk_load_async(void* dst, const void* src, unsigned bytes, uint64_t* bar,
+                                                unsigned extra = 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes + extra)
                  : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(dst)),

@@ -56,6 +56,8 @@ def load() -> ctypes.CDLL:
     vp = ctypes.c_void_p
     lib.hvp_batch_wait_test.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
     lib.hvp_batch_wait_test.restype = ctypes.c_int
+    lib.hvp_cache_wait_test.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+    lib.hvp_cache_wait_test.restype = ctypes.c_int
     lib.hvp_num_gates.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.hvp_num_gates.restype = ctypes.c_int
     lib.hvp_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HVPConfig), _dp, _dp]
@@ -228,6 +230,11 @@ class Context:
         keys = ["K", "passes", "window", "checkpoint_stride", "launches_per_hvp", "device_mib",
                 "tiles_per_cta", "ctas_per_sample", "threads", "variant"]
         return dict(zip(keys, list(info)))
+
+    def cache_wait_test(self, extra_bytes: int, spin_limit: int = 0):
+        """hvp_cache_wait_test: extra_bytes=16 makes the forward-cache copy waits
+        of the next calls run out after spin_limit polls."""
+        self._check(self._lib.hvp_cache_wait_test(self._h, extra_bytes, spin_limit))
 
     def close(self):
         if getattr(self, "_h", None):

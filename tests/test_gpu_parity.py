@@ -290,3 +290,24 @@ def test_forward_cache_schedule_against_recompute_and_oracle(threads):
             res[recompute] = r1
     assert rel(res[False][1], res[True][1]) < 2 * TOL["c64"]
     assert rel(res[False][2], res[True][2]) < 2 * TOL["c64"]
+
+
+def test_expired_cache_copy_wait_is_reported_and_context_stays_usable():
+    # Every forward-cache copy barrier expects 16 bytes more than its copy
+    # brings, so no wait completes: each gives up after 1000 polls, the call
+    # reports HVP_ETIMEOUT, and after restoring normal operation the same
+    # context evaluates correctly.
+    w = make_workload(10, 6, 2, seed=13)
+    o, phi = _oracle(w)
+    with native.Context(10, 6, w.psi1q, w.Uref, window=8) as ctx:
+        assert ctx.plan_info()["checkpoint_stride"] == 0
+        ctx.cache_wait_test(16, 1000)
+        with pytest.raises(native.HVPError) as e:
+            ctx.hvp(w.G, w.V)
+        assert e.value.code == native.HVP_ETIMEOUT
+        ctx.cache_wait_test(0, 0)
+        _check(ctx, w, o, TOL["c64"])
+    with native.Context(10, 6, w.psi1q, w.Uref, window=8, recompute=True) as ctx:
+        with pytest.raises(native.HVPError) as e:
+            ctx.cache_wait_test(16, 1000)
+        assert e.value.code == native.HVP_EINVAL
