@@ -70,6 +70,10 @@ extern "C" {
                              pass with G^-1 instead of keeping the states
                              before every gate in device memory (see
                              checkpoint_stride below)                         */
+#define HVP_MULTI_DIR 128 /* size the forward cache for two tangent
+                             directions (24 bytes per amplitude per gate), so
+                             that hvp_hvp_multi evaluates directions in pairs
+                             sharing one sweep; windows of at most 11 qubits */
 
 typedef struct hvp_ctx hvp_ctx;
 
@@ -172,6 +176,26 @@ int hvp_loss_grad(hvp_ctx *ctx, const double *G, double *loss, double *grad);
  * Blocks until the results are on the host. */
 int hvp_hvp(hvp_ctx *ctx, const double *G, const double *V, double *loss,
             double *grad, double *hvp);
+
+/* HVPs along n_dir directions at the same gates (Sec. 4: the truncated-CG
+ * inner loop and the dense Hessian of App. G evaluate many HVPs at one G).
+ * With HVP_MULTI_DIR and the forward cache, directions go through the sweep
+ * in pairs: the states psi, the co-states phi and the environments E are
+ * computed once per pair and only the tangent states and DE sums per
+ * direction (Eq. dfis, Eq. dbis, Eq. Dpsi); an odd last direction, and every
+ * direction of other contexts, take one sweep each.
+ *   G    : host, K*32 doubles; V : host, n_dir*K*32 doubles (direction d at
+ *          offset d*K*32);
+ *   loss, grad : host (may be NULL), as for hvp_hvp;
+ *   hvp  : host, n_dir*K*32 doubles (may be NULL), Euclidean or Riemannian.
+ * Blocks until the results are on the host. */
+int hvp_hvp_multi(hvp_ctx *ctx, const double *G, int n_dir, const double *V,
+                  double *loss, double *grad, double *hvp);
+
+/* The same on device pointers, stream-ordered on the context's stream. */
+int hvp_hvp_multi_dev(hvp_ctx *ctx, const double *G_dev, int n_dir,
+                      const double *V_dev, double *loss_dev, double *grad_dev,
+                      double *hvp_dev);
 
 /* Stream-ordered variants on device memory (for framework integration):
  * inputs and outputs are device pointers of the same sizes as above; V_dev

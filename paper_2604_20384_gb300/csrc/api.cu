@@ -79,6 +79,15 @@ struct hvp_ctx {
     size_t cache_slot = 0;     // bytes of one slot (tangent elements)
     void* d_chain = nullptr;   // forward states between passes (cache schedule)
     unsigned copy_wait_limit = 0, copy_extra_bytes = 0;   // hvp_cache_wait_test
+    // two tangent directions per sweep (HVP_MULTI_DIR with the forward cache)
+    bool pair = false;
+    double2* d_V2 = nullptr;
+    void* d_mats2 = nullptr;
+    double* d_partial2 = nullptr;
+    double* d_env2 = nullptr;
+    double* d_res2 = nullptr;
+    double* h_res2 = nullptr;
+    cudaGraphExec_t gexec_pair = nullptr;
     void* d_x = nullptr;       // unfused forward states
     double* d_partial = nullptr;
     double* d_env = nullptr;
@@ -310,6 +319,100 @@ int enqueue_unfused(hvp_ctx* c, bool tan, int* launches) {
     return HVP_OK;
 }
 
+// One pass of the two-direction schedule (both directions' tangents in one
+// sweep, forward cache of 24 bytes per amplitude per gate).
+int pair_pass(hvp_ctx* c, int p, int mode) {
+    TiledArgs a{};
+    a.pass = c->d_pass + p;
+    a.gates = c->d_gates;
+    a.mats = reinterpret_cast<const Mats32*>(c->d_mats);
+    a.mats2 = reinterpret_cast<const Mats32*>(c->d_mats2);
+    a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
+    a.xin = c->d_chain;
+    a.xout = c->d_chain;
+    a.phi = reinterpret_cast<const float2*>(c->d_phi);
+    a.cin = c->d_co;
+    a.cout = c->d_co;
+    a.partial = c->d_partial;
+    a.partial2 = c->d_partial2;
+    a.cache = c->d_cache;
+    a.cache_slot_bytes = ((size_t)1 << c->cfg.n) * c->cfg.n_samples * 24;
+    a.status = c->d_status;
+    a.copy_wait_limit = c->copy_wait_limit;
+    a.copy_extra_bytes = c->copy_extra_bytes;
+    a.n = c->cfg.n;
+    a.n_samples = c->cfg.n_samples;
+    a.mode = mode;
+    a.tiles_per_cta = c->tiles_per_cta;
+    a.cx_count = c->cx_count;
+    const int ng = (int)c->plan.passes[p].gates.size();
+    CUDA_TRY(c, launch_pair(a, c->w, std::max(ng, 1), c->stream));
+    return HVP_OK;
+}
+
+PostArgs post_args(hvp_ctx* c, double* partial, double* env, const double2* V, double* res) {
+    PostArgs p{};
+    p.partial = partial;
+    p.env = env;
+    p.G = c->d_G;
+    p.V = V;
+    p.T = reinterpret_cast<double2*>(res + c->off_T());
+    p.Omega = reinterpret_cast<double2*>(res + c->off_Om());
+    p.loss = res;
+    p.grad_e = reinterpret_cast<double2*>(res + c->off_ge());
+    p.hvp_e = reinterpret_cast<double2*>(res + c->off_he());
+    p.grad_r = reinterpret_cast<double2*>(res + c->off_gr());
+    p.hvp_r = reinterpret_cast<double2*>(res + c->off_hr());
+    p.K = c->K;
+    p.n_samples = c->cfg.n_samples;
+    p.cx_count = c->cx_count;
+    p.tangent = 1;
+    p.frobenius = (c->cfg.flags & HVP_FROBENIUS) ? 1 : 0;
+    return p;
+}
+
+// Loss, gradient and the HVPs along d_V and d_V2 in one sweep pair: results
+// of direction 1 in d_res, of direction 2 in d_res2.
+int enqueue_pair(hvp_ctx* c) {
+    int rc;
+    const int P = c->P;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, launch_prep(c->d_G, c->d_V, c->d_mats, false, c->K, c->d_status, c->stream));
+    CUDA_TRY(c, launch_prep(c->d_G, c->d_V2, c->d_mats2, false, c->K, c->d_status, c->stream));
+    for (int p = 0; p < P; ++p)
+        if ((rc = pair_pass(c, p, (p == 0 ? M_GEN : 0) | M_FWD | (p + 1 < P ? M_STORE_F : 0)))) return rc;
+    for (int p = P - 1; p >= 0; --p)
+        if ((rc = pair_pass(c, p, M_BWD | (p == P - 1 ? M_LOAD_PHI : 0) | (p > 0 ? M_STORE_B : 0)))) return rc;
+    CUDA_TRY(c, launch_post(post_args(c, c->d_partial, c->d_env, c->d_V, c->d_res), c->stream));
+    CUDA_TRY(c, launch_post(post_args(c, c->d_partial2, c->d_env2, c->d_V2, c->d_res2), c->stream));
+    return HVP_OK;
+}
+
+int run_pair(hvp_ctx* c) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(c, cudaStreamIsCapturing(c->stream, &cap));
+    if ((c->cfg.flags & HVP_NO_GRAPH) || cap != cudaStreamCaptureStatusNone) return enqueue_pair(c);
+    if (!c->gexec_pair) {
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_pair(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(c, HVP_ECUDA, fmt("graph capture failed: %s", cudaGetErrorString(e)));
+        e = cudaGraphInstantiate(&c->gexec_pair, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->gexec_pair = nullptr;
+            return fail(c, HVP_ECUDA, fmt("graph instantiation failed: %s", cudaGetErrorString(e)));
+        }
+    }
+    CUDA_TRY(c, cudaGraphLaunch(c->gexec_pair, c->stream));
+    return HVP_OK;
+}
+
 int enqueue_all(hvp_ctx* c, bool tan) {
     int L = 0, rc;
     CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
@@ -424,11 +527,14 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (ns < 1) return fail(c, HVP_EINVAL, "n_samples must be >= 1");
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
     if (cfg->flags &
-        ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS | HVP_RECOMPUTE))
+        ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS | HVP_RECOMPUTE |
+          HVP_MULTI_DIR))
         return fail(c, HVP_EINVAL, "unknown flag bits");
     if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
     if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))
         return fail(c, HVP_EINVAL, "window must be 0 (auto) or in [6, 12]");
+    if ((cfg->flags & HVP_MULTI_DIR) && cfg->window > 11)
+        return fail(c, HVP_EINVAL, "HVP_MULTI_DIR needs a window of at most 11 qubits (two-direction tiles)");
     if (cfg->threads != 0 && cfg->threads != 128 && cfg->threads != 256 && cfg->threads != 512)
         return fail(c, HVP_EINVAL, "threads must be 0 (auto), 128, 256 or 512");
     if (cfg->variant < 0 || cfg->variant > 3) return fail(c, HVP_EINVAL, "variant must be 0 (auto), 1, 2 or 3");
@@ -462,7 +568,8 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if ((cfg->flags & HVP_AUTOTUNE) && !c->unfused) {
         std::vector<int> windows;
         for (int wdw : {12, 11, 10})
-            if (wdw <= n || windows.empty()) windows.push_back(std::min(wdw, n));
+            if ((wdw <= n || windows.empty()) && !((cfg->flags & HVP_MULTI_DIR) && wdw > 11))
+                windows.push_back(std::min(wdw, n));
         std::sort(windows.begin(), windows.end());
         windows.erase(std::unique(windows.begin(), windows.end()), windows.end());
         std::vector<double> eye(32 * (size_t)c->K, 0.0), res_g(32 * (size_t)c->K), res_h(32 * (size_t)c->K);
@@ -521,7 +628,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         c->P = 0;
     } else {
         CUDA_TRY(c, tiled_set_smem_limits());
-        c->w = std::min(n, tuned.window ? tuned.window : 12);
+        c->w = std::min(n, tuned.window ? tuned.window : ((cfg->flags & HVP_MULTI_DIR) ? 11 : 12));
         c->threads = tuned.threads ? tuned.threads : 256;
         c->variant = tuned.variant ? tuned.variant : 1;
         if ((rc = make_plan(n, L, c->w, std::min(kLowBits, c->w - 1), c->plan))) return fail(c, rc, "planning failed");
@@ -537,7 +644,9 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if ((rc = dalloc(c, &c->d_mats, (c->dbl ? sizeof(Mats64) : sizeof(Mats32)) * (size_t)c->K))) return rc;
     if ((rc = dalloc(c, &c->d_psi1q, ctype * 2 * (size_t)n * ns))) return rc;
     if ((rc = dalloc(c, &c->d_phi, ctype * dim * ns))) return rc;
-    if ((rc = dalloc(c, &c->d_co, state_elt(c) * dim * ns))) return rc;
+    const bool multi = (cfg->flags & HVP_MULTI_DIR) && !c->unfused;
+    // two-direction sweeps keep (phi, dphi_1, dphi_2): 24 bytes per amplitude
+    if ((rc = dalloc(c, &c->d_co, (multi ? 24 : state_elt(c)) * dim * ns))) return rc;
     if ((rc = dalloc(c, (void**)&c->d_partial, 64 * sizeof(double) * (size_t)c->K * ns * c->cx_count))) return rc;
     if ((rc = dalloc(c, (void**)&c->d_env, 64 * sizeof(double) * (size_t)c->K * ns))) return rc;
     c->res_len = c->off_hr() + 32 * (size_t)c->K;
@@ -569,16 +678,29 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         // for a checkpoint stride, the scalar kernels are selected, the cached
         // backward pass fits in shared memory and the cache plus the chained
         // boundary states fit in 85 % of the free device memory.
-        const size_t slot = 16 * dim * ns;
+        const size_t slot = (multi ? 24 : 16) * dim * ns;
         const bool cache_fits = !(tuned.flags & HVP_RECOMPUTE) && cfg->checkpoint_stride == 0 && c->variant == 1 &&
                                 (c->threads == 128 || c->threads == 256) &&
                                 tiled_cached_smem_bytes(true, c->w, c->threads, c->max_gates) <= 227 * 1024 &&
-                                (double)slot * c->K + (double)sbytes <= 0.85 * (double)free_b;
+                                (!multi || pair_smem_bytes(true, c->w, 256, c->max_gates) <= 227 * 1024) &&
+                                (double)slot * c->K + (multi ? 1.5 : 1.0) * (double)sbytes <= 0.85 * (double)free_b;
         if (cache_fits) {
             if ((rc = dalloc(c, &c->d_cache, slot * (size_t)c->K))) return rc;
-            if ((rc = dalloc(c, &c->d_chain, sbytes))) return rc;
+            if ((rc = dalloc(c, &c->d_chain, (multi ? 24 : 16) * dim * ns))) return rc;
             c->cache = true;
             c->cache_slot = slot;
+            if (multi) {   // second direction's matrices, records and results
+                CUDA_TRY(c, pair_set_smem_limits());
+                if ((rc = dalloc(c, (void**)&c->d_V2, 16 * 16 * (size_t)c->K))) return rc;
+                if ((rc = dalloc(c, &c->d_mats2, sizeof(Mats32) * (size_t)c->K))) return rc;
+                if ((rc = dalloc(c, (void**)&c->d_partial2, 64 * sizeof(double) * (size_t)c->K * ns * c->cx_count)))
+                    return rc;
+                if ((rc = dalloc(c, (void**)&c->d_env2, 64 * sizeof(double) * (size_t)c->K * ns))) return rc;
+                if ((rc = dalloc(c, (void**)&c->d_res2, sizeof(double) * c->res_len))) return rc;
+                CUDA_TRY(c, cudaMemset(c->d_res2, 0, sizeof(double) * c->res_len));
+                CUDA_TRY(c, cudaMallocHost((void**)&c->h_res2, sizeof(double) * c->res_len));
+                c->pair = true;
+            }
             c->stride = 1;
             c->s0_last = 0;
             c->ckpt.assign(P + 1, nullptr);
@@ -827,6 +949,100 @@ int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* lo
     return HVP_OK;
 }
 
+int hvp_hvp_multi_dev(hvp_ctx* c, const double* G_dev, int n_dir, const double* V_dev, double* loss_dev,
+                      double* grad_dev, double* hvp_dev) {
+    if (!c) return HVP_EINVAL;
+    if (!G_dev || !V_dev || n_dir < 1) return fail(c, HVP_EINVAL, "hvp_hvp_multi_dev: NULL input or n_dir < 1");
+    if (c->batch) return fail(c, HVP_EINVAL, "hvp_hvp_multi_dev: not available for a batch context");
+    const size_t n32 = 32 * (size_t)c->K;
+    const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
+    const size_t off_h = riem ? c->off_hr() : c->off_he();
+    int d = 0;
+    if (c->pair) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+        for (; d + 1 < n_dir; d += 2) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_V, V_dev + d * n32, sizeof(double) * n32, cudaMemcpyDeviceToDevice,
+                                        c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_V2, V_dev + (d + 1) * n32, sizeof(double) * n32,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            int rc = run_pair(c);
+            if (rc) return rc;
+            if (hvp_dev) {
+                CUDA_TRY(c, cudaMemcpyAsync(hvp_dev + d * n32, c->d_res + off_h, sizeof(double) * n32,
+                                            cudaMemcpyDeviceToDevice, c->stream));
+                CUDA_TRY(c, cudaMemcpyAsync(hvp_dev + (d + 1) * n32, c->d_res2 + off_h, sizeof(double) * n32,
+                                            cudaMemcpyDeviceToDevice, c->stream));
+            }
+            if (d == 0) {
+                if (loss_dev)
+                    CUDA_TRY(c, cudaMemcpyAsync(loss_dev, c->d_res, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+                if (grad_dev)
+                    CUDA_TRY(c, cudaMemcpyAsync(grad_dev, c->d_res + (riem ? c->off_gr() : c->off_ge()),
+                                                sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+            }
+        }
+    }
+    for (; d < n_dir; ++d) {   // one direction per sweep
+        int rc = hvp_hvp_dev(c, G_dev, V_dev + d * n32, d == 0 ? loss_dev : nullptr, d == 0 ? grad_dev : nullptr,
+                             hvp_dev ? hvp_dev + d * n32 : nullptr);
+        if (rc) return rc;
+    }
+    return HVP_OK;
+}
+
+int hvp_hvp_multi(hvp_ctx* c, const double* G, int n_dir, const double* V, double* loss, double* grad,
+                  double* hvp) {
+    if (!c) return HVP_EINVAL;
+    if (!G || !V || n_dir < 1) return fail(c, HVP_EINVAL, "hvp_hvp_multi: NULL input or n_dir < 1");
+    if (c->batch) return fail(c, HVP_EINVAL, "hvp_hvp_multi: not available for a batch context");
+    const size_t n32 = 32 * (size_t)c->K;
+    if (!all_finite(G, n32) || !all_finite(V, n32 * n_dir)) return fail(c, HVP_ENONFINITE, "G or V is not finite");
+    const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
+    int d = 0;
+    if (c->pair) {
+        std::memcpy(c->h_in, G, sizeof(double) * n32);
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_G, c->h_in, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
+        for (; d + 1 < n_dir; d += 2) {
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // h_in is reused
+            std::memcpy(c->h_in + n32, V + d * n32, sizeof(double) * n32);
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_V, c->h_in + n32, sizeof(double) * n32, cudaMemcpyHostToDevice,
+                                        c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_V2, V + (d + 1) * n32, sizeof(double) * n32, cudaMemcpyHostToDevice,
+                                        c->stream));
+            int rc = run_pair(c);
+            if (rc) return rc;
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_res, c->d_res, sizeof(double) * c->res_len, cudaMemcpyDeviceToHost,
+                                        c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_res2, c->d_res2, sizeof(double) * c->res_len, cudaMemcpyDeviceToHost,
+                                        c->stream));
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            if (*c->h_status & 2) return fail(c, HVP_ETIMEOUT, "a bounded wait for a forward-cache copy expired");
+            if (*c->h_status) return fail(c, HVP_ENONFINITE, "a gate is singular or not finite");
+            const double* g = c->h_res + (riem ? c->off_gr() : c->off_ge());
+            const double* h1 = c->h_res + (riem ? c->off_hr() : c->off_he());
+            const double* h2 = c->h_res2 + (riem ? c->off_hr() : c->off_he());
+            if (!all_finite(c->h_res, c->off_ge() + n32) || !all_finite(g, n32) || !all_finite(h1, n32) ||
+                !all_finite(h2, n32))
+                return fail(c, HVP_ENONFINITE, "non-finite result");
+            if (d == 0) {
+                if (loss) *loss = c->h_res[0];
+                if (grad) std::memcpy(grad, g, sizeof(double) * n32);
+            }
+            if (hvp) {
+                std::memcpy(hvp + d * n32, h1, sizeof(double) * n32);
+                std::memcpy(hvp + (d + 1) * n32, h2, sizeof(double) * n32);
+            }
+        }
+    }
+    for (; d < n_dir; ++d) {
+        int rc = call_impl(c, G, V + d * n32, d == 0 ? loss : nullptr, d == 0 ? grad : nullptr,
+                           hvp ? hvp + d * n32 : nullptr);
+        if (rc) return rc;
+    }
+    return HVP_OK;
+}
+
 int hvp_profile(hvp_ctx* c, const double* G_dev, const double* V_dev, int max_launches, float* ms, int* kind,
                 double* flops, double* bytes) {
     if (!c || !G_dev || max_launches < 0) return HVP_EINVAL;
@@ -936,6 +1152,10 @@ int hvp_cache_wait_test(hvp_ctx* c, int extra_bytes, long long spin_limit) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    if (c->gexec_pair) {
+        cudaGraphExecDestroy(c->gexec_pair);
+        c->gexec_pair = nullptr;
+    }
     return HVP_OK;
 }
 
@@ -948,6 +1168,8 @@ void hvp_free(hvp_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& g : c->gexec)
         if (g) cudaGraphExecDestroy(g);
+    if (c->gexec_pair) cudaGraphExecDestroy(c->gexec_pair);
+    if (c->h_res2) cudaFreeHost(c->h_res2);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_in) cudaFreeHost(c->h_in);
     if (c->h_res) cudaFreeHost(c->h_res);

@@ -103,6 +103,8 @@ struct TiledArgs {
                                  // (sample, tile) one block of 2^w elements in shared-memory order
     size_t cache_slot_bytes;     // bytes of one cache slot (2^n * N_s elements)
     int* status;                 // bit 2: a bounded wait for a cache copy gave up
+    const Mats32* mats2;         // second direction's matrices (two-direction passes)
+    double* partial2;            // second direction's records (two-direction passes)
     unsigned copy_wait_limit;    // polls before a cache-copy wait gives up (0: the default)
     unsigned copy_extra_bytes;   // test of the bounded waits: bytes the copy barriers expect
                                  // beyond what arrives (0 in normal use)
@@ -124,6 +126,13 @@ cudaError_t launch_tiled_cached(const TiledArgs& a, bool tangent, int w, int thr
                                 cudaStream_t st);
 size_t tiled_cached_smem_bytes(bool tangent, int w, int threads, int max_gates);
 cudaError_t tiled_set_smem_limits();
+// Two tangent directions per sweep in the forward-cache schedule (pair.cu):
+// forward passes (mode M_FWD) writing a cache of (psi, dpsi_1, dpsi_2), 24
+// bytes per amplitude per gate, and backward passes (mode M_BWD) reading it;
+// 256 threads.
+cudaError_t launch_pair(const TiledArgs& a, int w, int max_gates, cudaStream_t st);
+size_t pair_smem_bytes(bool bwd, int w, int threads, int max_gates);
+cudaError_t pair_set_smem_limits();
 
 // Unfused (one launch per gate) kernels, real type R = float or double.
 cudaError_t unfused_init(bool dbl, const void* psi1q, void* x, int n, int ns, bool tangent, cudaStream_t st);

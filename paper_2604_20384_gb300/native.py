@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hvp.h")
 HVP_OK, HVP_EINVAL, HVP_ENOMEM, HVP_ECUDA, HVP_ETIMEOUT, HVP_ENONFINITE = 0, -1, -2, -3, -4, -5
 HVP_C64, HVP_C128 = 0, 1
 HVP_RIEMANNIAN, HVP_PHI_GIVEN, HVP_UNFUSED, HVP_NO_GRAPH, HVP_AUTOTUNE, HVP_FROBENIUS = 1, 2, 4, 8, 16, 32
-HVP_RECOMPUTE = 64
+HVP_RECOMPUTE, HVP_MULTI_DIR = 64, 128
 KINDS = {0: "prep", 1: "pass_fwd", 2: "pass_turnaround", 3: "pass_bwd", 4: "gate_init", 5: "gate_fwd",
          6: "gate_load_phi", 7: "gate_bwd", 8: "post"}
 OUT = dict(T=1, Omega=2, grad_e=3, hvp_e=4, grad_r=5, hvp_r=6, loss=7, env=8)
@@ -68,6 +68,10 @@ def load() -> ctypes.CDLL:
     lib.hvp_hvp.restype = ctypes.c_int
     lib.hvp_hvp_dev.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.hvp_hvp_dev.restype = ctypes.c_int
+    lib.hvp_hvp_multi.argtypes = [vp, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
+    lib.hvp_hvp_multi.restype = ctypes.c_int
+    lib.hvp_hvp_multi_dev.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp]
+    lib.hvp_hvp_multi_dev.restype = ctypes.c_int
     lib.hvp_get.argtypes = [vp, ctypes.c_int, _dp]
     lib.hvp_get.restype = ctypes.c_int
     lib.hvp_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
@@ -149,7 +153,7 @@ class Context:
                  riemannian: bool = False, phi_given: bool = False, unfused: bool = False,
                  graphs: bool = True, checkpoint_stride: int = 0, window: int = 0, threads: int = 0,
                  variant: int = 0, autotune: bool = False, frobenius: bool = False, recompute: bool = False,
-                 device: int = 0, stream: int | None = None):
+                 multi_dir: bool = False, device: int = 0, stream: int | None = None):
         self._lib = load()
         psi1q = np.asarray(psi1q)
         self.n, self.n_layers, self.n_samples = n, n_layers, int(psi1q.shape[0])
@@ -157,7 +161,7 @@ class Context:
         flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
                  | (HVP_UNFUSED if unfused else 0) | (0 if graphs else HVP_NO_GRAPH)
                  | (HVP_AUTOTUNE if autotune else 0) | (HVP_FROBENIUS if frobenius else 0)
-                 | (HVP_RECOMPUTE if recompute else 0))
+                 | (HVP_RECOMPUTE if recompute else 0) | (HVP_MULTI_DIR if multi_dir else 0))
         cfg = HVPConfig(n, n_layers, self.n_samples, HVP_C128 if precision == "c128" else HVP_C64, flags,
                         checkpoint_stride, window, threads, variant, device, stream)
         self._psi = _f64(psi1q)
@@ -189,6 +193,25 @@ class Context:
         self._check(self._lib.hvp_hvp(self._h, _ptr(G), _ptr(V), _ptr(loss), _ptr(grad), _ptr(hv)))
         return (float(loss[0]), grad.view(np.complex128).reshape(self.K, 4, 4),
                 hv.view(np.complex128).reshape(self.K, 4, 4))
+
+    def hvp_multi(self, G, Vs):
+        """(loss, grad, [HVP along each direction]) at the same gates
+        (hvp_hvp_multi); Vs: (n_dir, K, 4, 4)."""
+        G = _f64(G)
+        Vs = np.asarray(Vs)
+        nd = int(Vs.shape[0])
+        V = _f64(Vs)
+        loss = np.zeros(1)
+        grad = np.zeros(32 * self.K)
+        hv = np.zeros(32 * self.K * nd)
+        self._check(self._lib.hvp_hvp_multi(self._h, _ptr(G), nd, _ptr(V), _ptr(loss), _ptr(grad), _ptr(hv)))
+        return (float(loss[0]), grad.view(np.complex128).reshape(self.K, 4, 4),
+                hv.view(np.complex128).reshape(nd, self.K, 4, 4))
+
+    def hvp_multi_dev(self, G_ptr: int, n_dir: int, V_ptr: int, loss_ptr: int | None, grad_ptr: int | None,
+                      hvp_ptr: int | None):
+        """Stream-ordered hvp_hvp_multi_dev on device pointers."""
+        self._check(self._lib.hvp_hvp_multi_dev(self._h, G_ptr, n_dir, V_ptr, loss_ptr, grad_ptr, hvp_ptr))
 
     def hvp_dev(self, G_ptr: int, V_ptr: int | None, loss_ptr: int | None, grad_ptr: int | None,
                 hvp_ptr: int | None):
