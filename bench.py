@@ -184,6 +184,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the unfused FP64 comparison sweep")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-circuit measurement")
+    ap.add_argument("--no-multi", action="store_true", help="skip the two-directions-per-sweep measurement")
     ap.add_argument("--samples", type=int, default=64,
                     help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
@@ -413,6 +414,42 @@ def main():
             "persistent_ctas": binfo["ctas"], "launches_per_step": binfo["launches_per_hvp"],
             "window": binfo["window"], "window_choice": "autotuned among 12, 11, 10 at set-up",
             "achieved_tflops": amp_gates * 384 / (b_ms / 1e3) / 1e12}
+
+    # ------------------- two directions at the same gates per sweep (f1 line)
+    if not args.no_multi and rank == 0:
+        from paper_2604_20384_gb300.inputs import random_direction
+
+        wm = make_workload(20, 16, 32, seed=0)
+        Vs = np.stack([wm.V, random_direction(wm.K, wm.G, seed=5)])
+        mstream = torch.cuda.Stream(device=dev)
+        Gm = torch.from_numpy(wm.G.view(np.float64).reshape(-1).copy()).to(dev)
+        Vm = torch.from_numpy(Vs.view(np.float64).reshape(-1).copy()).to(dev)
+        hm = torch.zeros(2 * 32 * wm.K, dtype=torch.float64, device=dev)
+
+        def _time_two(**kw):
+            with native.Context(wm.n, wm.n_layers, wm.psi1q, wm.Uref, device=local, stream=mstream.cuda_stream,
+                                **kw) as cm:
+                for _ in range(3):
+                    cm.hvp_multi_dev(Gm.data_ptr(), 2, Vm.data_ptr(), None, None, hm.data_ptr())
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(mstream)
+                for _ in range(10):
+                    cm.hvp_multi_dev(Gm.data_ptr(), 2, Vm.data_ptr(), None, None, hm.data_ptr())
+                e1.record(mstream)
+                torch.cuda.synchronize(dev)
+                return e0.elapsed_time(e1) / 10, cm.plan_info()
+
+        pair_ms, pinfo = _time_two(window=11, multi_dir=True)
+        same_ms, _ = _time_two(window=11)
+        best_ms, binfo = _time_two()
+        line["two_directions"] = {
+            "workload": "n=20 L=16 N_s=32 (K=152), two directions at the same gates per call",
+            "value": 2000.0 / pair_ms, "unit": "HVPs/s", "ms_per_call": pair_ms,
+            "window": pinfo["window"], "device_mib": pinfo["device_mib"],
+            "one_direction_sweeps_same_window": {"value": 2000.0 / same_ms, "ms_per_call": same_ms},
+            "one_direction_sweeps_default_plan": {"value": 2000.0 / best_ms, "ms_per_call": best_ms,
+                                                  "window": binfo["window"]}}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
