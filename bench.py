@@ -194,6 +194,8 @@ def main():
                     help="recompute forward states inside window passes instead of caching every gate's")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library defaults (or --threads/--variant/--window) instead of autotuning at set-up")
+    ap.add_argument("--multi", action="store_true",
+                    help="with --quick: time two directions per call in a two-direction (HVP_MULTI_DIR) context")
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (for profiler captures)")
     args = ap.parse_args()
@@ -223,20 +225,31 @@ def main():
     dev = torch.device("cuda", local)
 
     w = make_workload(**dict(WORKLOAD, n_samples=args.samples))
-    autotune = not (args.no_autotune or args.threads or args.variant or args.window)
+    multi = args.multi and args.quick
+    autotune = not (args.no_autotune or args.threads or args.variant or args.window or multi)
     stream = torch.cuda.Stream(device=dev)
     ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
                          stream=stream.cuda_stream, threads=args.threads, variant=args.variant,
-                         window=args.window, autotune=autotune, recompute=args.recompute)
+                         window=args.window, autotune=autotune, recompute=args.recompute, multi_dir=multi)
     K = w.K
     G_dev = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
-    V_dev = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
+    if multi:
+        from paper_2604_20384_gb300.inputs import random_direction
+
+        Vs = np.stack([w.V, random_direction(K, w.G, seed=5)])
+        V_dev = torch.from_numpy(Vs.view(np.float64).reshape(-1).copy()).to(dev)
+    else:
+        V_dev = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
     loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
     grad_dev = torch.zeros(32 * K, dtype=torch.float64, device=dev)
-    hvp_dev = torch.zeros(32 * K, dtype=torch.float64, device=dev)
+    hvp_dev = torch.zeros(32 * K * (2 if multi else 1), dtype=torch.float64, device=dev)
     torch.cuda.synchronize(dev)
 
     def step():
+        if multi:
+            ctx.hvp_multi_dev(G_dev.data_ptr(), 2, V_dev.data_ptr(), loss_dev.data_ptr(), grad_dev.data_ptr(),
+                              hvp_dev.data_ptr())
+            return
         ctx.hvp_dev(G_dev.data_ptr(), V_dev.data_ptr(), loss_dev.data_ptr(), grad_dev.data_ptr(),
                     hvp_dev.data_ptr())
 
@@ -270,8 +283,9 @@ def main():
     value = world * 1000.0 / ms
     if args.quick:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "HVPs/s", "ms_per_step": ms,
-                              "n_samples": args.samples, "quick": True, "plan": info, "clocks": clocks}),
+            print(json.dumps({"metric": METRIC, "value": value * (2 if multi else 1), "unit": "HVPs/s",
+                              "ms_per_step": ms, "n_samples": args.samples, "quick": True,
+                              "directions_per_step": 2 if multi else 1, "plan": info, "clocks": clocks}),
                   flush=True)
         ctx.close()
         if dist:
