@@ -25,14 +25,23 @@ def tangent_basis(G) -> np.ndarray:
     return B
 
 
-def riemannian_hessian(hvp_fn, G) -> np.ndarray:
+def riemannian_hessian(hvp_fn, G, hvp_multi_fn=None, chunk: int = 64) -> np.ndarray:
     """Dense (16K x 16K) matrix in the Pauli tangent basis. hvp_fn(G, V)
     returns the Riemannian HVP H_R[V] as a (K, 4, 4) array (for example a
-    context created with riemannian=True: lambda G, V: ctx.hvp(G, V)[2])."""
+    context created with riemannian=True: lambda G, V: ctx.hvp(G, V)[2]).
+    With hvp_multi_fn(G, Vs) -> (n_dir, K, 4, 4) (e.g. a context with
+    riemannian=True and multi_dir=True: lambda G, Vs: ctx.hvp_multi(G, Vs)[2])
+    the columns are evaluated `chunk` directions per call, which the library
+    sends through its sweeps in pairs."""
     B = tangent_basis(G)
     n = B.shape[0]
     Bf = B.reshape(n, -1)
     H = np.zeros((n, n))
+    if hvp_multi_fn is not None:
+        for j0 in range(0, n, chunk):
+            cols = np.asarray(hvp_multi_fn(G, B[j0:j0 + chunk])).reshape(-1, Bf.shape[1])
+            H[:, j0:j0 + cols.shape[0]] = np.real(Bf.conj() @ cols.T)
+        return H
     for j in range(n):
         col = np.asarray(hvp_fn(G, B[j])).reshape(-1)
         H[:, j] = np.real(Bf.conj() @ col)

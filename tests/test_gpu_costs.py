@@ -67,3 +67,7 @@ def test_dense_riemannian_hessian_spectrum_on_gpu():
     assert np.max(np.abs(H - H.T)) < 1e-5 * np.max(np.abs(H))
     ev, evo = spectrum(H), spectrum(Ho)
     assert np.max(np.abs(ev - evo)) < 1e-5 * np.max(np.abs(evo))
+    # the same columns from direction pairs per sweep (hvp_hvp_multi)
+    with native.Context(n, L, w.psi1q, w.Uref, riemannian=True, multi_dir=True) as c:
+        Hm = riemannian_hessian(None, w.G, hvp_multi_fn=lambda G, Vs: c.hvp_multi(G, Vs)[2], chunk=17)
+    assert rel(Hm, Ho) < TOL
