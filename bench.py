@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -36,11 +37,20 @@ KERNEL_SOURCES = ["paper_2604_20384_gb300/csrc/tiled.cu", "paper_2604_20384_gb30
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_n20_L16_Ns64.json")
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without comments and blank lines (string literals in the
+    kernel sources hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the code (comments stripped) of the window-pass kernel sources."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()
 
 

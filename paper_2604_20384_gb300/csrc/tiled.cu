@@ -16,16 +16,21 @@
 //       E_k  += sum_a conj(a_i) psi^[k-1]_j
 //       DE_k += sum_a conj(b_i) psi^[k-1]_j + conj(a_i) dpsi^[k-1]_j
 //       b <- G_k^dag b + V_k^dag a ,  a <- G_k^dag a
-// The forward state psi^[k-1] is recomputed with G^-1 inside the pass; at pass
-// boundaries it comes from the forward checkpoint, so recomputation error does
-// not build up over the whole circuit.
+// Recompute schedule: the forward state psi^[k-1] is recomputed with G^-1
+// inside the pass; at pass boundaries it comes from the forward checkpoint,
+// so recomputation error does not build up over the whole circuit. Forward-
+// cache schedule: psi^[k-1], dpsi^[k-1] are read from the cache.
 //
-// Two kernels: a forward-only kernel (small register footprint: two CTAs per
-// SM at 256 threads, four at 128) and a backward kernel (forward part of the
-// turnaround pass included; 255 registers: one CTA per SM at 256 threads,
-// two at 128). Arithmetic forms, chosen at run time: scalar FP32 FMAs
-// (variant 1), packed fma.rn.f32x2 with gate matrices pre-expanded to
-// {m.re, m.re, -m.im, m.im} so that one complex multiply-add is two packed
+// Kernels: a forward kernel (small register footprint: two CTAs per SM at
+// 256 threads, four at 128), optionally writing the forward cache (the
+// states before every gate, as Alg. 1 keeps them); a recomputing backward
+// kernel (forward part of the turnaround pass included; 255 registers: one
+// CTA per SM at 256 threads, two at 128); and a backward kernel that reads
+// the forward cache by bulk copies instead of recomputing (tiled_bwdc_kernel,
+// 24 instead of 36 complex multiply-adds per amplitude per gate).
+// Arithmetic forms of the recompute schedule, chosen at run time: scalar
+// FP32 FMAs (variant 1), packed fma.rn.f32x2 with gate matrices pre-expanded
+// to {m.re, m.re, -m.im, m.im} so that one complex multiply-add is two packed
 // FMAs (variant 2), or scalar with two groups per thread iteration in the
 // backward pass (variant 3).
 //

@@ -1,6 +1,7 @@
 // Device helpers of the window-pass kernels, shared by the per-pass kernels
-// (tiled.cu) and the persistent batch kernel (batch.cu). See tiled.cu for the
-// arithmetic of a pass.
+// (tiled.cu), the two-direction kernels (pair.cu) and the persistent batch
+// kernel (batch.cu): tile I/O, bulk copies with mbarriers, gate arithmetic,
+// warp reductions. See tiled.cu for the arithmetic of a pass.
 #pragma once
 
 #include "internal.h"
