@@ -185,6 +185,40 @@ def run_reference(args, rank, world):
     return 0
 
 
+def batch_line(native, make_workload, torch, dev, local, n_circuits: int, reps: int) -> dict:
+    """Batched uneven circuits (n ~ U{8..16}, L ~ U{4..20}, N_s log-uniform in
+    32..512, seed 0; the first n_circuits of the 64): one persistent launch per
+    call, window width autotuned at set-up."""
+    import numpy as np
+    from paper_2604_20384_gb300.inputs import uneven_batch_shapes
+
+    shapes = uneven_batch_shapes(64, seed=0)[:n_circuits]
+    bws = [make_workload(n, L, ns, sd) for (n, L, ns, sd) in shapes]
+    bstream = torch.cuda.Stream(device=dev)
+    with native.BatchContext([(x.n, x.n_layers, x.psi1q, x.Uref) for x in bws], device=local,
+                             stream=bstream.cuda_stream, autotune=True) as bctx:
+        Gb = torch.from_numpy(np.concatenate([x.G for x in bws]).view(np.float64).reshape(-1).copy()).to(dev)
+        Vb = torch.from_numpy(np.concatenate([x.V for x in bws]).view(np.float64).reshape(-1).copy()).to(dev)
+        for _ in range(3):
+            bctx.hvp_dev(Gb.data_ptr(), Vb.data_ptr(), None, None, None)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bstream)
+        for _ in range(reps):
+            bctx.hvp_dev(Gb.data_ptr(), Vb.data_ptr(), None, None, None)
+        e1.record(bstream)
+        torch.cuda.synchronize(dev)
+        b_ms = e0.elapsed_time(e1) / reps
+        binfo = bctx.plan_info()
+    amp_gates = sum((1 << x.n) * x.n_samples * x.K for x in bws)
+    return {"workload": f"{n_circuits} circuits, n~U{{8..16}}, L~U{{4..20}}, N_s log-uniform 32..512 (seed 0)",
+            "value": 1000.0 / b_ms, "unit": "batch HVP evaluations/s", "ms_per_step": b_ms,
+            "circuit_hvps_per_s": n_circuits * 1000.0 / b_ms, "work_items": binfo["items"],
+            "persistent_ctas": binfo["ctas"], "launches_per_step": binfo["launches_per_hvp"],
+            "window": binfo["window"], "window_choice": "autotuned among 12, 11, 10 at set-up",
+            "achieved_tflops": amp_gates * 384 / (b_ms / 1e3) / 1e12}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,6 +240,10 @@ def main():
                     help="use the library defaults (or --threads/--variant/--window) instead of autotuning at set-up")
     ap.add_argument("--multi", action="store_true",
                     help="with --quick: time two directions per call in a two-direction (HVP_MULTI_DIR) context")
+    ap.add_argument("--quick-batch", type=int, default=0, metavar="C",
+                    help="only time the batched line on its first C circuits (for profiler captures)")
+    ap.add_argument("--quick-fp64", action="store_true",
+                    help="only time the unfused complex128 sweep at --samples (for profiler captures)")
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (for profiler captures)")
     args = ap.parse_args()
@@ -233,8 +271,33 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.quick_batch:
+        if rank == 0:
+            print(json.dumps(dict(batch_line(native, make_workload, torch, dev, local, args.quick_batch,
+                                             max(args.steps, 1)), quick=True)), flush=True)
+        return 0
 
     w = make_workload(**dict(WORKLOAD, n_samples=args.samples))
+    if args.quick_fp64:
+        fstream = torch.cuda.Stream(device=dev)
+        Gf = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
+        Vf = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
+        with native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c128", device=local,
+                            stream=fstream.cuda_stream) as c2:
+            for _ in range(args.warmup):
+                c2.hvp_dev(Gf.data_ptr(), Vf.data_ptr(), None, None, None)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(fstream)
+            for _ in range(max(args.steps, 1)):
+                c2.hvp_dev(Gf.data_ptr(), Vf.data_ptr(), None, None, None)
+            e1.record(fstream)
+            torch.cuda.synchronize(dev)
+            f_ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        if rank == 0:
+            print(json.dumps({"fp64_unfused": True, "n_samples": args.samples, "ms_per_step": f_ms,
+                              "value": 1000.0 / f_ms, "unit": "HVPs/s", "quick": True}), flush=True)
+        return 0
     multi = args.multi and args.quick
     autotune = not (args.no_autotune or args.threads or args.variant or args.window or multi)
     stream = torch.cuda.Stream(device=dev)
@@ -409,35 +472,7 @@ def main():
 
     # ------------------------------- batched uneven circuits (secondary line)
     if not args.no_batch and rank == 0:
-        from paper_2604_20384_gb300.inputs import uneven_batch_shapes
-
-        shapes = uneven_batch_shapes(64, seed=0)
-        bws = [make_workload(n, L, ns, sd) for (n, L, ns, sd) in shapes]
-        bstream = torch.cuda.Stream(device=dev)
-        with native.BatchContext([(x.n, x.n_layers, x.psi1q, x.Uref) for x in bws], device=local,
-                                 stream=bstream.cuda_stream, autotune=True) as bctx:
-            Gb = torch.from_numpy(np.concatenate([x.G for x in bws]).view(np.float64).reshape(-1).copy()).to(dev)
-            Vb = torch.from_numpy(np.concatenate([x.V for x in bws]).view(np.float64).reshape(-1).copy()).to(dev)
-            for _ in range(3):
-                bctx.hvp_dev(Gb.data_ptr(), Vb.data_ptr(), None, None, None)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(bstream)
-            nb = 10
-            for _ in range(nb):
-                bctx.hvp_dev(Gb.data_ptr(), Vb.data_ptr(), None, None, None)
-            e1.record(bstream)
-            torch.cuda.synchronize(dev)
-            b_ms = e0.elapsed_time(e1) / nb
-            binfo = bctx.plan_info()
-        amp_gates = sum((1 << x.n) * x.n_samples * x.K for x in bws)
-        line["batched_uneven"] = {
-            "workload": "64 circuits, n~U{8..16}, L~U{4..20}, N_s log-uniform 32..512 (seed 0)",
-            "value": 1000.0 / b_ms, "unit": "batch HVP evaluations/s", "ms_per_step": b_ms,
-            "circuit_hvps_per_s": 64 * 1000.0 / b_ms, "work_items": binfo["items"],
-            "persistent_ctas": binfo["ctas"], "launches_per_step": binfo["launches_per_hvp"],
-            "window": binfo["window"], "window_choice": "autotuned among 12, 11, 10 at set-up",
-            "achieved_tflops": amp_gates * 384 / (b_ms / 1e3) / 1e12}
+        line["batched_uneven"] = batch_line(native, make_workload, torch, dev, local, 64, 10)
 
     # ------------------- two directions at the same gates per sweep (f1 line)
     if not args.no_multi and rank == 0:

@@ -180,22 +180,32 @@ __global__ void __launch_bounds__(kUT) u_bwd_kernel(const typename MatsR<R>::T* 
         if constexpr (TAN) {
             PairC<C>* x = reinterpret_cast<PairC<C>*>(xv) + off;
             PairC<C>* c = reinterpret_cast<PairC<C>*>(cv) + off;
-            C p[4], d[4], A[4], B[4], pp[4], tt[4], dp[4], nA[4], nB[4];
+            // Forward states first (written back before the co-states are
+            // loaded), so that fewer values are live beside the 32 complex
+            // accumulators: the complex128 form would not fit in registers.
+            C pp[4], dp[4], A[4], B[4], nA[4], nB[4];
+            {
+                C p[4], tt[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { p[j] = x[idx[j]].s; d[j] = x[idx[j]].t; A[j] = c[idx[j]].s; B[j] = c[idx[j]].t; }
-            matvec4(Gi, p, pp);
+                for (int j = 0; j < 4; ++j) p[j] = x[idx[j]].s;
+                matvec4(Gi, p, pp);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                tt[r] = d[r];
+                for (int r = 0; r < 4; ++r) {
+                    tt[r] = x[idx[r]].t;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    C mv = V[r * 4 + j];
-                    mv.x = -mv.x;
-                    mv.y = -mv.y;
-                    cmac(tt[r], mv, pp[j]);
+                    for (int j = 0; j < 4; ++j) {
+                        C mv = V[r * 4 + j];
+                        mv.x = -mv.x;
+                        mv.y = -mv.y;
+                        cmac(tt[r], mv, pp[j]);
+                    }
                 }
+                matvec4(Gi, tt, dp);
             }
-            matvec4(Gi, tt, dp);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) x[idx[r]] = PairC<C>{pp[r], dp[r]};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { A[j] = c[idx[j]].s; B[j] = c[idx[j]].t; }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -211,7 +221,7 @@ __global__ void __launch_bounds__(kUT) u_bwd_kernel(const typename MatsR<R>::T* 
 #pragma unroll
                 for (int j = 0; j < 4; ++j) cmac(nB[r], Vh[r * 4 + j], A[j]);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) { x[idx[r]] = PairC<C>{pp[r], dp[r]}; c[idx[r]] = PairC<C>{nA[r], nB[r]}; }
+            for (int r = 0; r < 4; ++r) c[idx[r]] = PairC<C>{nA[r], nB[r]};
         } else {
             C* x = reinterpret_cast<C*>(xv) + off;
             C* c = reinterpret_cast<C*>(cv) + off;
