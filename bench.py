@@ -417,6 +417,7 @@ def main():
     fwd = by_kind.get("pass_fwd", {"ms": 0.0, "flops": 0.0, "launches": 0})
     all_ms = sum(by_kind[k]["ms"] for k in by_kind if k.startswith("pass_"))
     all_fl = sum(by_kind[k]["flops"] for k in by_kind if k.startswith("pass_"))
+    all_by = sum(by_kind[k]["bytes"] for k in by_kind if k.startswith("pass_"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": recorded_traffic(info),
                 "kernel": (f"tiled_bwdc_kernel<tangent, {info['threads']} threads> (backward window passes "
@@ -434,7 +435,12 @@ def main():
                                       "frac": all_fl / (all_ms / 1e3) / 1e12 / alu_peak},
                 "hbm": {"achieved_gbs": p_by / (p_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
                         "frac": (p_by / (p_ms / 1e3) / 1e9) / peaks.get("hbm_gbs", 6800.0),
-                        "peak_source": src}}
+                        "peak_source": src},
+                # every window pass of the step: the schedule's algorithmic bytes (state I/O and, with
+                # the forward cache, 16 B per amplitude per gate written and read back) over their time
+                "step_hbm": {"achieved_gbs": all_by / (all_ms / 1e3) / 1e9,
+                             "frac": (all_by / (all_ms / 1e3) / 1e9) / peaks.get("hbm_gbs", 6800.0),
+                             "bytes_per_step": all_by}}
 
     line = {"metric": METRIC, "value": value, "unit": "HVPs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

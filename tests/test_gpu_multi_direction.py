@@ -19,14 +19,18 @@ def _dirs(w, count, seed):
     return np.stack([w.V] + [random_direction(w.K, w.G, seed=seed + i) for i in range(count - 1)])
 
 
-@pytest.mark.parametrize("window,riemannian", [(10, False), (11, False), (9, True)])
-def test_direction_pairs_match_oracle(window, riemannian):
+@pytest.mark.parametrize("window,riemannian,frobenius", [(10, False, False), (11, False, False), (9, True, False),
+                                                         (10, False, True)])
+def test_direction_pairs_match_oracle(window, riemannian, frobenius):
     n, L, ns = 14, 8, 16
     w = make_workload(n, L, ns, seed=51)
     Vs = _dirs(w, 3, 90)                     # one pair and one single direction
     phi = oracle.reference_states(n, L, w.Uref, w.psi1q)
     key_g, key_h = ("grad_r", "hvp_r") if riemannian else ("grad", "hvp")
-    with native.Context(n, L, w.psi1q, w.Uref, window=window, riemannian=riemannian, multi_dir=True) as ctx:
+    if frobenius:
+        key_g, key_h = "grad_f", "hvp_f"
+    with native.Context(n, L, w.psi1q, w.Uref, window=window, riemannian=riemannian, multi_dir=True,
+                        frobenius=frobenius) as ctx:
         info = ctx.plan_info()
         assert info["checkpoint_stride"] == 0 and info["window"] == window and info["passes"] > 1
         loss, grad, hv = ctx.hvp_multi(w.G, Vs)
@@ -34,7 +38,8 @@ def test_direction_pairs_match_oracle(window, riemannian):
     for d, V in enumerate(Vs):
         o = oracle.evaluate(n, L, w.G, V, w.psi1q, phi)
         if d == 0:
-            assert abs((1 - loss) - (1 - o["loss"])) <= TOL * abs(1 - o["loss"])
+            lo = o["loss_f"] if frobenius else o["loss"]
+            assert abs((1 - loss) - (1 - lo)) <= TOL * abs(1 - lo)
             assert rel(grad, o[key_g]) < TOL
         assert rel(hv[d], o[key_h]) < TOL, (d, rel(hv[d], o[key_h]))
         assert rel(hv[d], single[d][2]) < 2 * TOL
