@@ -219,6 +219,76 @@ def batch_line(native, make_workload, torch, dev, local, n_circuits: int, reps: 
             "achieved_tflops": amp_gates * 384 / (b_ms / 1e3) / 1e12}
 
 
+def _time_calls(torch, stream, dev, fn, reps: int, warm: int = 2) -> float:
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def n12_precision_line(native, make_workload, torch, dev, local) -> dict:
+    """n = 12, L = 8, N_s = 256: complex64 window passes with FP64 accumulation
+    next to the complex128 per-gate sweep, each timed and compared with the
+    other (the oracle comparison of both is in the GPU tests)."""
+    import numpy as np
+
+    w = make_workload(12, 8, 256, seed=0)
+    st = torch.cuda.Stream(device=dev)
+    G = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
+    V = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
+    out = {}
+    res = {}
+    for prec in ("c64", "c128"):
+        with native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision=prec, device=local,
+                            stream=st.cuda_stream) as c:
+            ms = _time_calls(torch, st, dev, lambda: c.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None), 20)
+            res[prec] = c.hvp(w.G, w.V)
+            out[prec] = {"value": 1000.0 / ms, "unit": "HVPs/s", "ms_per_step": ms}
+    g64, h64 = res["c64"][1], res["c64"][2]
+    g128, h128 = res["c128"][1], res["c128"][2]
+    out["c64_vs_c128"] = {"grad_rel": float(np.linalg.norm(g64 - g128) / np.linalg.norm(g128)),
+                          "hvp_rel": float(np.linalg.norm(h64 - h128) / np.linalg.norm(h128)),
+                          "loss_abs": abs(res["c64"][0] - res["c128"][0])}
+    out["workload"] = "n=12 L=8 N_s=256 (K=44), 8 MiB per state set (L2-resident)"
+    return out
+
+
+def n26_autograd_line(make_workload, torch, dev, local) -> dict:
+    """n = 26, L = 24, N_s = 8 through the torch.autograd layer: loss and
+    gradient by the adjoint sweep (HSLoss backward) and the HVP by forward-
+    over-reverse (jvp of HSGrad); the forward cache does not fit at this
+    size, so forward states are recomputed from boundary checkpoints."""
+    from paper_2604_20384_gb300 import autograd as hsa
+
+    w = make_workload(26, 24, 8, seed=0)
+    cost = hsa.HSCost(w.n, w.n_layers, w.psi1q, w.Uref, device=local)
+    try:
+        G = torch.from_numpy(w.G).to(dev)
+        V = torch.from_numpy(w.V).to(dev)
+        cur = torch.cuda.current_stream(dev)
+
+        def grad_step():
+            Gr = G.clone().requires_grad_(True)
+            hsa.loss(Gr, cost).backward()
+
+        ms_g = _time_calls(torch, cur, dev, grad_step, 3, warm=1)
+        ms_h = _time_calls(torch, cur, dev, lambda: hsa.hvp(G, V, cost), 3, warm=1)
+        info = cost.ctx.plan_info()
+    finally:
+        cost.close()
+    return {"workload": "n=26 L=24 N_s=8 (K=300, 8 GiB per state set), torch.autograd layer",
+            "loss_grad_backward": {"value": 1000.0 / ms_g, "unit": "evaluations/s", "ms_per_step": ms_g},
+            "hvp_forward_over_reverse": {"value": 1000.0 / ms_h, "unit": "HVPs/s", "ms_per_step": ms_h},
+            "passes": info["passes"], "checkpoint_stride": info["checkpoint_stride"],
+            "device_mib": info["device_mib"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -229,6 +299,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the unfused FP64 comparison sweep")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-circuit measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the two-directions-per-sweep measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the n=12 precision and n=26 autograd lines")
     ap.add_argument("--samples", type=int, default=64,
                     help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
@@ -390,6 +461,21 @@ def main():
     T_gpu, Om_gpu = ctx.get("T"), ctx.get("Omega")
     E_gpu, DE_gpu = ctx.get("env")
 
+    # ------------------------------- loss and gradient only (no tangent sweep; after the
+    # per-sample outputs of the last HVP call were read)
+    for _ in range(3):
+        ctx.hvp_dev(G_dev.data_ptr(), None, loss_dev.data_ptr(), grad_dev.data_ptr(), None)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        ctx.hvp_dev(G_dev.data_ptr(), None, loss_dev.data_ptr(), grad_dev.data_ptr(), None)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    lg_ms = e0.elapsed_time(e1) / 10
+    loss_grad_line = {"workload": "n=20 L=16 N_s=64, loss and gradient only (Alg. 1 without tangents)",
+                      "value": world * 1000.0 / lg_ms, "unit": "evaluations/s", "ms_per_step": lg_ms}
+
     prof = ctx.profile(G_dev.data_ptr(), V_dev.data_ptr())
     kinds = prof["kind"]
     by_kind = {}
@@ -457,7 +543,7 @@ def main():
                        "l2": "inputs larger than L2 (512 MiB per state set, 129 MB L2)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": info["launches_per_hvp"] * args.steps,
-            "clocks": clocks, "per_kind": by_kind}
+            "clocks": clocks, "per_kind": by_kind, "loss_grad_only": loss_grad_line}
 
     # ------------------------------------------ unfused FP64 sweep, same GPU
     if not args.no_fp64 and rank == 0:
@@ -516,6 +602,11 @@ def main():
             "one_direction_sweeps_default_plan": {"value": 2000.0 / best_ms, "ms_per_call": best_ms,
                                                   "window": binfo["window"]}}
 
+    # --------------- n = 12 precision comparison and n = 26 autograd form
+    if not args.no_configs and rank == 0:
+        line["n12_precision"] = n12_precision_line(native, make_workload, torch, dev, local)
+        line["n26_autograd"] = n26_autograd_line(make_workload, torch, dev, local)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
         line["cpu_baseline"] = {k: v for k, v in cb.items() if k not in ("seconds_per_step", "steps", "oracle_out")}
@@ -531,8 +622,13 @@ def main():
             "samples": m, "tolerance": 1e-5,
             "T_rel": _rel(T_gpu[:m], o["T"]), "Omega_rel": _rel(Om_gpu[:m], o["Omega"]),
             "E_rel": _rel(E_gpu[:m], o["E"]), "DE_rel": _rel(DE_gpu[:m], o["DE"])}
+        pv = line["parity_vs_oracle"]
+        pv["pass"] = all(pv[k] < pv["tolerance"] for k in ("T_rel", "Omega_rel", "E_rel", "DE_rel"))
     if rank == 0:
         print(json.dumps(line), flush=True)
+        if not line.get("parity_vs_oracle", {}).get("pass", True):
+            print("bench: timed configuration disagrees with the oracle", file=sys.stderr, flush=True)
+            return 1
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -10,7 +10,10 @@ functions of the gate tensor G (complex128, shape (K, 4, 4), on the GPU).
   tangent sweep (forward-over-reverse, Eq. FoR); its backward applied to W
   returns H[W] as well (the Hessian is self-adjoint for Re<., .>).
 * ``hvp(G, V, cost)`` is the forward-mode derivative of ``HSGrad`` along V
-  (dual tensors of ``torch.autograd.forward_ad``).
+  (dual tensors of ``torch.autograd.forward_ad``). Since the tangent is
+  known before the primal is evaluated, the primal and its jvp come from one
+  tangent sweep (which returns the gradient as well) instead of an adjoint
+  sweep followed by a tangent sweep.
 
 All arithmetic runs in libhvp; tensors are passed as device pointers and the
 work is ordered against PyTorch's current stream with stream waits.
@@ -31,6 +34,8 @@ class HSCost:
         self.stream = torch.cuda.Stream(device=self.device)
         self.ctx = native.Context(n, n_layers, psi1q, ref, device=device, stream=self.stream.cuda_stream, **kw)
         self.K = self.ctx.K
+        self._fused_tangent = None   # set by hvp(): the tangent of the next HSGrad
+        self._fused_hv = None        # (tangent, H[tangent]) left by that HSGrad forward
 
     def _run(self, G: torch.Tensor, V: torch.Tensor | None, want_hvp: bool):
         if G.dtype != torch.complex128 or G.shape != (self.K, 4, 4) or G.device != self.device:
@@ -85,7 +90,12 @@ class HSGrad(torch.autograd.Function):
 
     @staticmethod
     def forward(G, cost):
-        return cost.loss_grad(G)[1]
+        V = cost._fused_tangent
+        if V is None:
+            return cost.loss_grad(G)[1]
+        _, grad, hv = cost.loss_grad_hvp(G, V)
+        cost._fused_hv = (V, hv)
+        return grad
 
     @staticmethod
     def setup_context(ctx, inputs, output):
@@ -96,6 +106,9 @@ class HSGrad(torch.autograd.Function):
 
     @staticmethod
     def jvp(ctx, V, _dcost):
+        stash, ctx.cost._fused_hv = ctx.cost._fused_hv, None
+        if stash is not None and stash[0].data_ptr() == V.data_ptr() and stash[0].shape == V.shape:
+            return stash[1]
         (G,) = ctx.saved_tensors
         return ctx.cost.loss_grad_hvp(G, V)[2]
 
@@ -120,7 +133,13 @@ def hvp(G: torch.Tensor, V: torch.Tensor, cost: HSCost):
     derivative of grad C along V."""
     import torch.autograd.forward_ad as fwAD
 
+    T = V.detach().to(G.dtype).contiguous()
     with fwAD.dual_level():
-        out = HSGrad.apply(fwAD.make_dual(G.detach(), V.detach().to(G.dtype)), cost)
+        cost._fused_tangent = T
+        try:
+            out = HSGrad.apply(fwAD.make_dual(G.detach(), T), cost)
+        finally:
+            cost._fused_tangent = None
+            cost._fused_hv = None
         primal, tangent = fwAD.unpack_dual(out)
     return primal, tangent
