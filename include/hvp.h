@@ -80,7 +80,7 @@ typedef struct hvp_ctx hvp_ctx;
 typedef struct {
     int n;                 /* qubits, 2..30                                    */
     int n_layers;          /* brickwall layers L >= 1                          */
-    int n_samples;         /* N_s >= 1                                         */
+    int n_samples;         /* N_s, 1..65535 (2^n * N_s at most 2^34)           */
     int precision;         /* HVP_C64 or HVP_C128                              */
     int flags;             /* HVP_* flags, or-ed                               */
     int checkpoint_stride; /* 0 = automatic: the forward states before every

@@ -525,6 +525,8 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (n < 2 || n > kMaxN) return fail(c, HVP_EINVAL, fmt("n = %d outside [2, %d]", n, kMaxN));
     if (L < 1) return fail(c, HVP_EINVAL, "n_layers must be >= 1");
     if (ns < 1) return fail(c, HVP_EINVAL, "n_samples must be >= 1");
+    if (ns > kMaxSamples)   // one grid row per sample in the window-pass launches
+        return fail(c, HVP_EINVAL, fmt("n_samples = %d above %d", ns, kMaxSamples));
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
     if (cfg->flags &
         ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS | HVP_RECOMPUTE |

@@ -10,6 +10,7 @@
 namespace hvp {
 
 constexpr int kMaxN = 30;            // qubits
+constexpr int kMaxSamples = 65535;   // samples of one context (grid rows of the window passes)
 constexpr int kMaxW = 14;            // local qubits per shared-memory tile
 constexpr int kMaxGatesPerPass = 64; // shared-memory budget of one window pass
 constexpr int kLowBits = 4;          // address bits every tile keeps contiguous (16 amplitudes)

@@ -95,6 +95,9 @@ def test_init_validates_arguments_before_cuda():
     cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 128, 2, 0, None)        # 128 threads: scalar arithmetic only
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
     assert b"128 threads" in lib.hvp_last_error(None)
+    cfg = native.HVPConfig(6, 3, 65536, 0, 0, 0, 0, 0, 0, 0, None)      # one grid row per sample: at most 65535
+    assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), native._ptr(psi), native._ptr(ref)) == native.HVP_EINVAL
+    assert b"n_samples = 65536" in lib.hvp_last_error(None)
     cfg = native.HVPConfig(6, 3, 2, 0, 0, 0, 0, 0, 0, 0, None)
     assert lib.hvp_init(ctypes.byref(h), ctypes.byref(cfg), None, native._ptr(ref)) == native.HVP_EINVAL
     bad = psi.copy()
