@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(NT, 1) pair_bwdc_kernel(TiledArgs a) {
     float* wred = reinterpret_cast<float*>(mats + ngates * 48);
     float* acc = wred + 2 * NW * NV;                               // [ngates][NV]
     uint64_t* bars = reinterpret_cast<uint64_t*>(acc + ngates * NV);
-    volatile int* stop = reinterpret_cast<volatile int*>(bars + 2);
+    volatile int* stop = reinterpret_cast<volatile int*>(bars + 2);   // [step parity]
     int2* guv = reinterpret_cast<int2*>(bars + 3);
 
     stage_pair_mats(mats, a, goff, ngates, 2, 4);
@@ -212,7 +212,8 @@ __global__ void __launch_bounds__(NT, 1) pair_bwdc_kernel(TiledArgs a) {
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
-        *stop = 0;
+        stop[0] = 0;
+        stop[1] = 0;
         fence_barrier_init();
     }
     __syncthreads();
@@ -246,7 +247,12 @@ __global__ void __launch_bounds__(NT, 1) pair_bwdc_kernel(TiledArgs a) {
         } else {
             pair_load<NT>(sb4, sb2, a.cin, A, tc, P->out_lo, P->out_hi, Lt);
         }
+        __syncthreads();   // the tile's co-states are in place before any warp starts a gate
 
+        // One barrier per gate, as in the one-direction cached kernel: a thread
+        // whose copy wait expires raises the stop flag of this step's parity and
+        // goes on with the stale buffer; the flag is read after the barrier that
+        // ends the step, which no later step's wait can precede.
         for (int i = 0; i < ngates; ++i) {
             const int g = ngates - 1 - i, b = i & 1;
             unsigned char* const cur = b ? buf1 : buf0;
@@ -254,11 +260,9 @@ __global__ void __launch_bounds__(NT, 1) pair_bwdc_kernel(TiledArgs a) {
                 par ^= 1u << b;
                 pend &= ~(1u << b);
             } else {
-                *stop = 1;
+                stop[b] = 1;
                 atomicOr(a.status, 2);
             }
-            __syncthreads();
-            if (*stop) break;
             const float4* c4 = reinterpret_cast<const float4*>(cur);
             const float2* c2 = reinterpret_cast<const float2*>(c4 + Lt);
             const float2* Gh = mats + (g * 3) * 16;
@@ -319,6 +323,7 @@ __global__ void __launch_bounds__(NT, 1) pair_bwdc_kernel(TiledArgs a) {
 #pragma unroll
             for (int k = 0; k < NV / 32; ++k) wr[lane * (NV / 32) + k] = red[k];
             __syncthreads();
+            if (stop[b]) break;
             if (tid == 0 && i + 2 < ngates) {
                 fence_proxy_async_smem();
                 bulk_load_async(cur, pair_cache_block(a, goff + g - 2, s, t, ng, Lt), bytes, &bars[b],
@@ -332,12 +337,12 @@ __global__ void __launch_bounds__(NT, 1) pair_bwdc_kernel(TiledArgs a) {
                 acc[g * NV + tid] += sum;
             }
         }
-        if (*stop) break;
+        if (stop[0] | stop[1]) break;
         if (mode & M_STORE_B) pair_store<NT>(a.cout, A, sb4, sb2, tc, P->in_lo, P->in_hi, Lt);
         __syncthreads();
     }
 
-    if (*stop) {
+    if (stop[0] | stop[1]) {
         if (tid == 0)
             for (int j = 0; j < 2; ++j)
                 if ((pend >> j) & 1u) mbar_wait_bounded(&bars[j], (par >> j) & 1u, wait_limit);

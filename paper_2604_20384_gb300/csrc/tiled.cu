@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
     float* wred = reinterpret_cast<float*>(mats + ngates * 2 * 16);
     float* acc = wred + 2 * NW * 64;                           // [ngates][NV] FP32 per CTA
     uint64_t* bars = reinterpret_cast<uint64_t*>(acc + ngates * NV);
-    volatile int* stop = reinterpret_cast<volatile int*>(bars + 2);
+    volatile int* stop = reinterpret_cast<volatile int*>(bars + 2);   // [step parity]
     int2* guv = reinterpret_cast<int2*>(bars + 3);            // [gate] shared-memory bits (u, v)
 
     const int which[2] = {2, 4};   // G^dag, V^dag
@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
-        *stop = 0;
+        stop[0] = 0;
+        stop[1] = 0;
         fence_barrier_init();
     }
     __syncthreads();
@@ -282,7 +283,14 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
         } else {
             load_tile<E, NT>(sb, reinterpret_cast<const E*>(a.cin), tc, ldlo, ldhi, Lt);
         }
+        __syncthreads();   // the tile's co-states are in place before any warp starts a gate
 
+        // One barrier per gate. Every thread waits for the cached states itself;
+        // a thread whose wait expires raises the stop flag of this step's parity
+        // and goes on with the stale buffer (its reads stay in bounds). The flag
+        // is read after the barrier that ends the step: only this step's waits
+        // can have set it (a wait of step i + 2 starts after the barrier of step
+        // i + 1), so every thread leaves at the same step.
         for (int i = 0; i < ngates; ++i) {
             const int g = ngates - 1 - i, b = i & 1;
             E* const cur = b ? buf1 : buf0;
@@ -290,11 +298,9 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
                 par ^= 1u << b;
                 pend &= ~(1u << b);
             } else {
-                *stop = 1;
+                stop[b] = 1;
                 atomicOr(a.status, 2);
             }
-            __syncthreads();
-            if (*stop) break;
             const int2 uv = guv[g];
             float red[NV];
 #pragma unroll
@@ -306,6 +312,7 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
 #pragma unroll
             for (int k = 0; k < NV / 32; ++k) wr[lane * (NV / 32) + k] = red[k];
             __syncthreads();
+            if (stop[b]) break;
             if (tid == 0 && i + 2 < ngates) {   // buffer b is free again: cached states two gates ahead
                 fence_proxy_async_smem();
                 bulk_load_async(cur, cache_tile<E>(a, goff + g - 2, s, t, ng, Lt), bytes, &bars[b], extra);
@@ -318,12 +325,12 @@ __global__ void __launch_bounds__(NT, 1) tiled_bwdc_kernel(TiledArgs a) {
                 acc[g * NV + tid] += sum;
             }
         }
-        if (*stop) break;
+        if (stop[0] | stop[1]) break;
         if (mode & M_STORE_B) store_tile<E, NT>(reinterpret_cast<E*>(a.cout), sb, tc, stlo, sthi, Lt);
         __syncthreads();
     }
 
-    if (*stop) {   // a copy did not arrive: let the ones still in flight land before the CTA ends
+    if (stop[0] | stop[1]) {   // a copy did not arrive: let the ones still in flight land before the CTA ends
         if (tid == 0)
             for (int j = 0; j < 2; ++j)
                 if ((pend >> j) & 1u) mbar_wait_bounded(&bars[j], (par >> j) & 1u, wait_limit);
