@@ -99,7 +99,9 @@ typedef struct {
     int variant;           /* arithmetic of the window-pass kernels: 1 scalar
                               FP32 FMA, 2 packed fma.rn.f32x2, 3 scalar with
                               two groups per thread iteration in the backward
-                              passes; 0 = auto                                 */
+                              passes; 0 = auto. The forward-cache schedule
+                              runs the scalar kernels: variants 2 and 3 select
+                              the recompute schedule                           */
     int device;            /* CUDA device ordinal                              */
     void *stream;          /* cudaStream_t for all work; NULL = own stream     */
 } hvp_config;
