@@ -134,6 +134,25 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def cpu_model() -> str:
+    """Host CPU model as lscpu reports it (x86 and Arm), else /proc/cpuinfo."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(w, steps=1, warmup=0, max_seconds=150.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     as many of the N_s samples as the host has cores, one thread each. Cost is
@@ -157,7 +176,7 @@ def cpu_baseline(w, steps=1, warmup=0, max_seconds=150.0):
         if sum(times) > max_seconds:
             break
     sec = statistics.median(times)
-    return dict(value=(m / w.n_samples) / sec, unit="HVPs/s", cores=m, kind="oracle",
+    return dict(value=(m / w.n_samples) / sec, unit="HVPs/s", cores=m, kind="oracle", cpu=cpu_model(),
                 sample=f"{m} of {w.n_samples} samples (n={w.n}, L={w.n_layers}), {m} threads, "
                        f"checkpoint stride {stride}; {sec:.2f} s per sample batch, scaled by {m}/{w.n_samples}",
                 seconds_per_step=sec, steps=len(times), oracle_out=out)
@@ -179,7 +198,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152)", "n": 20, "L": 16, "N_s": 64},
-            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu")},
             "e2e": {"value": cb["value"], "unit": "HVPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
