@@ -355,6 +355,68 @@ def test_frobenius_solution_point():
     assert np.max(np.abs(o["grad_fr"])) < 1e-13
 
 
+
+def _geodesic_loss_f(w, phi, X, t):
+    Gt = np.stack([w.G[k] @ expm_skew(t * X[k]) for k in range(w.K)])
+    return oracle.evaluate(w.n, w.n_layers, Gt, None, w.psi1q, phi)["loss_f"]
+
+
+def test_frobenius_riemannian_gradient_and_hvp_along_geodesics():
+    # App. F applied to Eq. Frobenius: along the geodesic t -> G exp(tX),
+    # d/dt C_F = Re<grad_R, GX> and d^2/dt^2 C_F = Re<GX, H_R[GX]> at t = 0,
+    # with H_R built from the Frobenius gradient (a slip to the HS gradient in
+    # the -V grad^dag G / 2 terms changes the second derivative). Away from the
+    # solution point, so that the gradient is not zero.
+    w = make_workload(5, 4, 5, seed=18)
+    phi = oracle.reference_states(5, 4, w.Uref, w.psi1q)
+    X = np.stack([w.G[k].conj().T @ w.V[k] for k in range(w.K)])    # skew-Hermitian
+    o = oracle.evaluate(5, 4, w.G, w.V, w.psi1q, phi)
+    assert np.linalg.norm(o["grad_fr"]) > 1e-2
+    h = 1e-3
+    c0 = _geodesic_loss_f(w, phi, X, 0.0)
+    cp, cm = _geodesic_loss_f(w, phi, X, h), _geodesic_loss_f(w, phi, X, -h)
+    cp2, cm2 = _geodesic_loss_f(w, phi, X, 2 * h), _geodesic_loss_f(w, phi, X, -2 * h)
+    d1 = (8 * (cp - cm) - (cp2 - cm2)) / (12 * h)
+    d2 = (-cp2 + 16 * cp - 30 * c0 + 16 * cm - cm2) / (12 * h * h)
+    assert abs(re_inner(o["grad_fr"], w.V) - d1) < 1e-9
+    assert abs(re_inner(w.V, o["hvp_fr"]) - d2) < 1e-6 * max(1.0, abs(d2))
+    # the Euclidean Frobenius HVP alone does not give the geodesic curvature:
+    # the App. F correction terms are needed (checks that the pin can fail)
+    assert abs(re_inner(w.V, o["hvp_f"]) - d2) > 1e-4 * max(1.0, abs(d2))
+
+
+def test_frobenius_riemannian_gradient_per_gate_directions():
+    # Re<grad_R, G_k X_k> for one gate at a time equals the first geodesic
+    # derivative of C_F moving that gate alone (pins every gate's block of
+    # grad_fr, not only its inner product with V).
+    w = make_workload(4, 3, 4, seed=19)
+    phi = oracle.reference_states(4, 3, w.Uref, w.psi1q)
+    o = oracle.evaluate(4, 3, w.G, w.V, w.psi1q, phi)
+    rng = np.random.default_rng(5)
+    h = 1e-3
+    for k in range(w.K):
+        A = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+        Xk = 0.5 * (A - A.conj().T)
+        X = np.zeros((w.K, 4, 4), complex)
+        X[k] = Xk
+        cp, cm = _geodesic_loss_f(w, phi, X, h), _geodesic_loss_f(w, phi, X, -h)
+        cp2, cm2 = _geodesic_loss_f(w, phi, X, 2 * h), _geodesic_loss_f(w, phi, X, -2 * h)
+        d1 = (8 * (cp - cm) - (cp2 - cm2)) / (12 * h)
+        assert abs(np.real(np.vdot(o["grad_fr"][k], w.G[k] @ Xk)) - d1) < 1e-10
+        S = w.G[k].conj().T @ o["grad_fr"][k]
+        assert np.max(np.abs(S + S.conj().T)) < 1e-13                # tangent at G_k
+
+
+def test_frobenius_riemannian_hessian_self_adjoint():
+    # <H_R u, v> = <u, H_R v> on tangent vectors, for the Frobenius cost too.
+    w = make_workload(6, 3, 6, seed=21)
+    phi = oracle.reference_states(6, 3, w.Uref, w.psi1q)
+    W = random_direction(w.K, w.G, seed=33)
+    a = oracle.evaluate(6, 3, w.G, w.V, w.psi1q, phi)["hvp_fr"]
+    b = oracle.evaluate(6, 3, w.G, W, w.psi1q, phi)["hvp_fr"]
+    assert abs(re_inner(W, a) - re_inner(w.V, b)) < 1e-12
+
+
 # ---------------------------------------------------------------- translation invariance (App. E)
 
 def test_translation_invariant_chain_rule():
