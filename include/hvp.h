@@ -31,7 +31,11 @@
  *
  * Errors: every int-returning call returns HVP_OK (0) or a negative code;
  * hvp_last_error gives a message. Calls on one context must not overlap;
- * distinct contexts are independent.
+ * distinct contexts are independent. A failed hvp_init / hvp_init_batch
+ * releases everything it allocated. For tests of that path, the environment
+ * variable HVP_DEVICE_ALLOC_CAP_MB caps the device memory one context (or
+ * batch) may allocate: an allocation beyond it fails with HVP_ENOMEM as if
+ * cudaMalloc had failed.
  *
  * Gates are not required to be unitary (finite differences evaluate G + hV);
  * they must be invertible, because the backward sweep recomputes earlier
@@ -74,6 +78,18 @@ extern "C" {
                              directions (24 bytes per amplitude per gate), so
                              that hvp_hvp_multi evaluates directions in pairs
                              sharing one sweep; windows of at most 11 qubits */
+#define HVP_TENSOR 256    /* fused-block schedule on the tensor cores: the gates
+                             are grouped into blocks of 5 neighbouring qubits
+                             (App. D's block-triangular [[B, 0], [dB, B]] per
+                             block), each block applied to all states as a
+                             real 128 x 128 GEMM with three TF32 products per
+                             FP32 product (tcgen05, sm_103a), the forward states
+                             at every block boundary kept in device memory
+                             ((blocks + 1) * 16 * 2^n * N_s bytes), the
+                             co-states weighted by T_s and Omega_s so that the
+                             block environments sum over samples. Needs
+                             complex64 and n >= 5; per-sample environments
+                             (HVP_OUT_ENV) are not formed                     */
 
 typedef struct hvp_ctx hvp_ctx;
 
@@ -159,7 +175,14 @@ int hvp_batch_wait_test(hvp_ctx *ctx, int dep_bias, long long spin_limit);
  * usable. extra_bytes = 0 with spin_limit = 0 restores normal operation.
  * Applies to the next calls (captured graphs are rebuilt). HVP_EINVAL if the
  * context does not run the forward cache (hvp_plan_info info[3] != 0) or an
- * argument is out of range. */
+ * argument is out of range.
+ * On a context with HVP_TENSOR the same call tests the bounded waits of the
+ * tensor-core passes: extra_bytes = 16 makes the barrier on which each tile
+ * waits for its MMAs expect one arrival more than the MMAs' commit delivers,
+ * and limits those waits to spin_limit polls (at least 1); every wait then
+ * gives up, the pass commits its MMAs in flight to a separate barrier, waits
+ * for them (bounded), frees its tensor memory and stops, and the next call
+ * returns HVP_ETIMEOUT. extra_bytes = 0 restores normal operation. */
 int hvp_cache_wait_test(hvp_ctx *ctx, int extra_bytes, long long spin_limit);
 
 /* Loss and gradient (Alg. 1 without tangents, Alg. 2 first two steps).
@@ -215,7 +238,8 @@ int hvp_hvp_dev(hvp_ctx *ctx, const double *G_dev, const double *V_dev,
  *   HVP_OUT_LOSS : 1 double;
  *   HVP_OUT_ENV : per-sample environments dT_s/dG_k and D(dT_s/dG_k)[V],
  *        N_s*K*32 complex (N_s*K*64 doubles; the 16 entries of E then the
- *        16 of DE per gate). */
+ *        16 of DE per gate); HVP_EINVAL with HVP_TENSOR, whose block
+ *        environments are summed over samples. */
 #define HVP_OUT_T 1
 #define HVP_OUT_OMEGA 2
 #define HVP_OUT_GRAD_E 3
@@ -232,8 +256,18 @@ int hvp_get(hvp_ctx *ctx, int what, double *out);
  *   states before every gate are cached), info[4] = kernel
  *   launches of the last hvp call, info[5] = device memory held by the
  *   context in MiB, info[6] = tiles per CTA, info[7] = CTAs per sample,
- *   info[8] = threads per CTA, info[9] = arithmetic variant. */
+ *   info[8] = threads per CTA, info[9] = arithmetic variant.
+ * With HVP_TENSOR: info[1] = number of fused blocks, info[2] = 5 (block
+ * qubits), info[3] = 0, info[6] = 0, info[7] = CTAs of the backward block
+ * passes, info[8] = 256, info[9] = 0 (TF32 tensor-core arithmetic). */
 int hvp_plan_info(const hvp_ctx *ctx, long long info[10]);
+
+/* Fused-block plan of the HVP_TENSOR schedule without a context or GPU (for
+ * tests and tools): block_of_gate[K] receives the block of each gate and
+ * block_qubit[j] the first of block j's five qubits (arrays of K entries,
+ * either may be NULL); returns the number of blocks, or HVP_EINVAL for
+ * n < 5. */
+int hvp_plan_blocks(int n, int n_layers, int *block_of_gate, int *block_qubit);
 
 /* Window-pass plan of a brickwall without a context or GPU (for tests and
  * tools): fills pass_of_gate[K] with the pass index of each gate and returns
@@ -262,14 +296,16 @@ int hvp_plan_brickwall(int n, int n_layers, int window, int low_bits, int *pass_
 #define HVP_K_GATE_PHI 6
 #define HVP_K_GATE_BWD 7
 #define HVP_K_POST 8
+#define HVP_K_BLOCK_FWD 9   /* one fused block applied forward (HVP_TENSOR)   */
+#define HVP_K_BLOCK_BWD 10  /* one fused block backward with its environment  */
 int hvp_profile(hvp_ctx *ctx, const double *G_dev, const double *V_dev, int max_launches,
                 float *ms, int *kind, double *flops, double *bytes);
 
 /* Loss, gradient and HVP without any device allocation, for callers that
  * cannot call cudaMalloc: code running inside a framework that owns the whole
- * device pool through its own allocator, a CUDA-graph replay harness whose
- * memory plan is frozen, or a host process under a strict memory budget. The
- * paper has no counterpart; it is an engineering entry point.
+ * device pool through its own allocator, or a host process under a strict
+ * device-memory budget. The paper has no counterpart; it is an engineering
+ * entry point.
  *
  * The work space is one static device array of HVP_NOALLOC_SCRATCH_BYTES that
  * every GPU which loads this library holds until the process exits. The
@@ -283,9 +319,11 @@ int hvp_profile(hvp_ctx *ctx, const double *G_dev, const double *V_dev, int max_
  * space of 2^n*N_s*8 + K*N_s*1024 + K*1680 + N_s*(16n + 32) bytes plus at
  * most 8 kB of tables and alignment, which must fit in
  * HVP_NOALLOC_SCRATCH_BYTES (16 MiB; e.g. n = 12, L = 8, N_s = 128 fits);
- * larger problems return HVP_EINVAL with a message in hvp_last_error(NULL). HVP_ENONFINITE reports a singular or
- * non-finite gate. The call waits for its own work (it reads back a status
- * word).
+ * larger problems return HVP_EINVAL with a message in hvp_last_error(NULL).
+ * HVP_ENONFINITE reports a singular or non-finite gate.
+ * The call is synchronous: it copies its small tables from host memory into
+ * the array, enqueues its kernels on `stream`, reads back a status word and
+ * waits for the stream before it returns.
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture. Every call reuses the same array, so
  * calls that overlap on the GPU (other threads, other streams) race; serialise

@@ -109,6 +109,21 @@ struct hvp_ctx {
     // batched contexts (hvp_init_batch)
     BatchImpl* batch = nullptr;
     int n_circuits = 0;
+    // fused-block schedule on the tensor cores (HVP_TENSOR)
+    bool tensor = false;
+    std::vector<BlockPlan> blocks;
+    int nb = 0, tc_ctas_fwd = 1, tc_ctas_bwd = 1, ovl_chunks = 1;
+    DevBlock* d_blocks = nullptr;
+    DevBlockGate* d_bgates = nullptr;
+    Mats64* d_mats64 = nullptr;     // FP64 G, G^-1, V, Y per gate (block post-processing)
+    uint32_t* d_ops = nullptr;      // per block: the operator record (integer slices and row scales)
+    std::vector<void*> tstate;      // forward states at the output of block j (float4 per amplitude)
+    double* d_rec = nullptr;        // per block and CTA: FP64 environment records (128 x 128)
+    double* d_psum = nullptr;       // per block: records summed over CTAs
+    double2* d_Ew = nullptr;        // per gate: sum_s conj(T_s) E_s
+    double2* d_DEw = nullptr;       // per gate: sum_s conj(Omega_s) E_s + conj(T_s) DE_s
+    double* d_ovl = nullptr;        // overlap partial sums
+    unsigned tc_wait_limit = 0, tc_barrier_extra = 0;   // hvp_cache_wait_test on a tensor context
 
     size_t off_T() const { return 2; }
     size_t off_Om() const { return 2 + 2 * (size_t)cfg.n_samples; }
@@ -150,6 +165,9 @@ int prof_mark(hvp_ctx* c, int kind, double flops, double bytes) {
 int dalloc(hvp_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return HVP_OK;
+    if (c->bytes + bytes > device_alloc_cap())
+        return fail(c, HVP_ENOMEM, fmt("device allocation of %zu bytes exceeds the cap HVP_DEVICE_ALLOC_CAP_MB "
+                                       "(%zu bytes held)", bytes, c->bytes));
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -413,9 +431,93 @@ int run_pair(hvp_ctx* c) {
     return HVP_OK;
 }
 
+// Fused-block schedule (HVP_TENSOR): FP64 gate and block preparation, the
+// forward block passes keeping the states at every block boundary, the
+// overlaps T_s, Omega_s, the backward block passes from the weighted
+// co-states (T_s phi_s, Omega_s phi_s) accumulating the block environments,
+// and the FP64 reduction to per-gate gradient and HVP blocks.
+int enqueue_tensor(hvp_ctx* c, bool tan) {
+    const int n = c->cfg.n, ns = c->cfg.n_samples, nb = c->nb;
+    const bool frob = (c->cfg.flags & HVP_FROBENIUS) != 0;
+    const double amps = (double)((size_t)1 << n) * ns;
+    const long long ncols = (long long)ns << (n - 5);
+    double2* T = reinterpret_cast<double2*>(c->d_res + c->off_T());
+    double2* Om = reinterpret_cast<double2*>(c->d_res + c->off_Om());
+    int rc, L = 0;
+    CUDA_TRY(c, launch_prep(c->d_G, tan ? c->d_V : nullptr, c->d_mats64, true, c->K, c->d_status, c->stream));
+    CUDA_TRY(c, launch_block_prep(c->d_blocks, c->d_bgates, nb, c->d_G, tan ? c->d_V : nullptr, c->d_ops,
+                                  c->d_status, c->stream));
+    if ((rc = prof_mark(c, HVP_K_PREP, 0.0, 0.0))) return rc;
+    L += 2;
+    // Tensor-pipe flops per amplitude and block: forward, two halves of the
+    // 128 x 64 operator x 4 components / 32 amplitudes, six bf16 slice
+    // products each (6144; half of it without tangents); backward, plus the
+    // environment GEMM, 128 x 128 x 4 / 32 with three TF32 products (3072).
+    const double fl_fwd = tan ? 6144.0 : 3072.0, fl_bwd = fl_fwd + 3072.0;
+    for (int j = 0; j < nb; ++j) {
+        TcbArgs a{};
+        a.ops = c->d_ops + (size_t)j * kOpWords;
+        a.xin = j ? reinterpret_cast<const float4*>(c->tstate[j - 1]) : nullptr;
+        a.xout = reinterpret_cast<float4*>(c->tstate[j]);
+        a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
+        a.status = c->d_status;
+        a.ncols = ncols;
+        a.n = n;
+        a.a = c->blocks[j].a;
+        a.mode = (j == 0 ? TCB_GEN : 0) | (tan ? 0 : TCB_NO_TANGENT);
+        a.wait_limit = c->tc_wait_limit;
+        a.barrier_extra = c->tc_barrier_extra;
+        CUDA_TRY(c, launch_tcb(a, false, c->tc_ctas_fwd, c->stream));
+        if ((rc = prof_mark(c, HVP_K_BLOCK_FWD, amps * fl_fwd, amps * (j ? 32.0 : 16.0)))) return rc;
+        ++L;
+    }
+    CUDA_TRY(c, launch_overlaps(reinterpret_cast<const float4*>(c->tstate[nb - 1]),
+                                reinterpret_cast<const float2*>(c->d_phi), c->d_ovl, T, Om, n, ns, c->ovl_chunks,
+                                c->stream));
+    if ((rc = prof_mark(c, HVP_K_POST, 0.0, amps * 24.0))) return rc;
+    L += 2;
+    for (int j = nb - 1; j >= 0; --j) {
+        TcbArgs a{};
+        a.ops = c->d_ops + (size_t)j * kOpWords;
+        a.xin = reinterpret_cast<const float4*>(c->d_co);
+        a.xout = reinterpret_cast<float4*>(c->d_co);
+        a.psi = j ? reinterpret_cast<const float4*>(c->tstate[j - 1]) : nullptr;
+        a.phi = reinterpret_cast<const float2*>(c->d_phi);
+        a.w1 = frob ? nullptr : T;
+        a.w2 = frob ? nullptr : Om;
+        a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
+        a.rec = c->d_rec + (size_t)j * c->tc_ctas_bwd * 16384;
+        a.status = c->d_status;
+        a.ncols = ncols;
+        a.n = n;
+        a.a = c->blocks[j].a;
+        a.mode = (j == nb - 1 ? TCB_LOAD_PHI : 0) | (j == 0 ? (TCB_GEN | TCB_NO_STORE) : 0) |
+                 (tan ? 0 : TCB_NO_TANGENT);
+        a.wait_limit = c->tc_wait_limit;
+        a.barrier_extra = c->tc_barrier_extra;
+        CUDA_TRY(c, launch_tcb(a, true, c->tc_ctas_bwd, c->stream));
+        const double by = (j == nb - 1 ? 8.0 : 16.0) + (j ? 16.0 : 0.0) + (j ? 16.0 : 0.0);
+        if ((rc = prof_mark(c, HVP_K_BLOCK_BWD, amps * fl_bwd, amps * by))) return rc;
+        ++L;
+    }
+    CUDA_TRY(c, launch_block_post(c->d_blocks, c->d_bgates, nb, c->d_rec, c->tc_ctas_bwd, c->d_psum, c->d_mats64,
+                                  c->d_Ew, c->d_DEw, tan ? 1 : 0, c->stream));
+    CUDA_TRY(c, launch_post_weighted(c->d_Ew, c->d_DEw, c->d_G, c->d_V, T,
+                                     reinterpret_cast<double2*>(c->d_res + c->off_ge()),
+                                     reinterpret_cast<double2*>(c->d_res + c->off_he()),
+                                     reinterpret_cast<double2*>(c->d_res + c->off_gr()),
+                                     reinterpret_cast<double2*>(c->d_res + c->off_hr()), c->d_res, c->K, ns,
+                                     tan ? 1 : 0, frob ? 1 : 0, c->stream));
+    if ((rc = prof_mark(c, HVP_K_POST, 0.0, 0.0))) return rc;
+    L += 4;
+    c->launches_per_call[tan ? 1 : 0] = L + 1;   // + the status reset
+    return HVP_OK;
+}
+
 int enqueue_all(hvp_ctx* c, bool tan) {
     int L = 0, rc;
     CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    if (c->tensor) return enqueue_tensor(c, tan);
     CUDA_TRY(c, launch_prep(c->d_G, tan ? c->d_V : nullptr, c->d_mats, c->dbl, c->K, c->d_status, c->stream));
     if ((rc = prof_mark(c, HVP_K_PREP, 0.0, 0.0))) return rc;
     ++L;
@@ -479,6 +581,33 @@ int compute_phi_from_uref(hvp_ctx* c, const double* uref) {
     const int n = c->cfg.n, ns = c->cfg.n_samples;
     CUDA_TRY(c, cudaMemcpyAsync(c->d_G, uref, 32 * sizeof(double) * c->K, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    if (c->tensor) {
+        // the forward block passes without tangents (the block operators of U_ref
+        // with dB = 0), then the states of the last boundary into phi
+        CUDA_TRY(c, launch_prep(c->d_G, nullptr, c->d_mats64, true, c->K, c->d_status, c->stream));
+        CUDA_TRY(c, launch_block_prep(c->d_blocks, c->d_bgates, c->nb, c->d_G, nullptr, c->d_ops, c->d_status,
+                                      c->stream));
+        for (int j = 0; j < c->nb; ++j) {
+            TcbArgs a{};
+            a.ops = c->d_ops + (size_t)j * kOpWords;
+            a.xin = j ? reinterpret_cast<const float4*>(c->tstate[j - 1]) : nullptr;
+            a.xout = reinterpret_cast<float4*>(c->tstate[j]);
+            a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
+            a.status = c->d_status;
+            a.ncols = (long long)ns << (n - 5);
+            a.n = n;
+            a.a = c->blocks[j].a;
+            a.mode = (j == 0 ? TCB_GEN : 0) | TCB_NO_TANGENT;
+            CUDA_TRY(c, launch_tcb(a, false, c->tc_ctas_fwd, c->stream));
+        }
+        CUDA_TRY(c, launch_extract_psi(reinterpret_cast<const float4*>(c->tstate[c->nb - 1]),
+                                       reinterpret_cast<float2*>(c->d_phi), ((size_t)1 << n) * ns, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (*c->h_status & 2) return fail(c, HVP_ETIMEOUT, "a bounded wait of a tensor-core pass expired");
+        if (*c->h_status) return fail(c, HVP_ENONFINITE, "U_ref contains a non-finite or singular gate");
+        return HVP_OK;
+    }
     CUDA_TRY(c, launch_prep(c->d_G, nullptr, c->d_mats, c->dbl, c->K, c->d_status, c->stream));
     if (c->unfused) {
         CUDA_TRY(c, unfused_init(c->dbl, c->d_psi1q, c->d_phi, n, ns, false, c->stream));
@@ -530,8 +659,12 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
     if (cfg->flags &
         ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS | HVP_RECOMPUTE |
-          HVP_MULTI_DIR))
+          HVP_MULTI_DIR | HVP_TENSOR))
         return fail(c, HVP_EINVAL, "unknown flag bits");
+    if ((cfg->flags & HVP_TENSOR) &&
+        (cfg->precision != HVP_C64 || (cfg->flags & (HVP_UNFUSED | HVP_MULTI_DIR | HVP_RECOMPUTE)) || n < 5))
+        return fail(c, HVP_EINVAL, "HVP_TENSOR needs complex64, n >= 5 and none of HVP_UNFUSED, HVP_MULTI_DIR, "
+                                   "HVP_RECOMPUTE");
     if (cfg->checkpoint_stride < 0) return fail(c, HVP_EINVAL, "checkpoint_stride must be >= 0");
     if (cfg->window != 0 && (cfg->window < 6 || cfg->window > 12))
         return fail(c, HVP_EINVAL, "window must be 0 (auto) or in [6, 12]");
@@ -592,11 +725,15 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
                 if (wdw <= 11) cands.push_back({wdw, 128, 1, 0});
             }
         }
+        // the fused-block tensor-core schedule (taken when its states fit)
+        const bool may_tensor = !(cfg->flags & (HVP_MULTI_DIR | HVP_RECOMPUTE)) && cfg->checkpoint_stride == 0 && n >= 5;
+        if (may_tensor) cands.push_back({0, 256, 0, 2});
         for (const auto& cand : cands) {
             const int wdw = cand[0], var = cand[2];
             hvp_config sc = *cfg;
-            sc.flags &= ~HVP_AUTOTUNE;
-            if (cand[3]) sc.flags |= HVP_RECOMPUTE;
+            sc.flags &= ~(HVP_AUTOTUNE | HVP_TENSOR);
+            if (cand[3] == 1) sc.flags |= HVP_RECOMPUTE;
+            if (cand[3] == 2) sc.flags |= HVP_TENSOR;
             sc.window = wdw >= n ? 0 : wdw;
             sc.threads = cand[1];
             sc.variant = var;
@@ -614,16 +751,30 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
                 tuned.window = sc.window;
                 tuned.threads = sc.threads;
                 tuned.variant = var;
-                tuned.flags = (cfg->flags & ~HVP_RECOMPUTE) | (sc.flags & HVP_RECOMPUTE);
+                tuned.flags = (cfg->flags & ~(HVP_RECOMPUTE | HVP_TENSOR)) | (sc.flags & (HVP_RECOMPUTE | HVP_TENSOR));
             }
         }
         cudaGetLastError();
-        c->cfg.flags = (c->cfg.flags & ~HVP_RECOMPUTE) | (tuned.flags & HVP_RECOMPUTE);
+        c->cfg.flags = (c->cfg.flags & ~(HVP_RECOMPUTE | HVP_TENSOR)) | (tuned.flags & (HVP_RECOMPUTE | HVP_TENSOR));
     }
+    c->tensor = (c->cfg.flags & HVP_TENSOR) != 0;
 
     // Plan.
     int rc;
-    if (c->unfused) {
+    if (c->tensor) {
+        CUDA_TRY(c, tcb_set_smem_limits());
+        if ((rc = make_block_plan(n, L, c->blocks))) return fail(c, rc, "block planning failed");
+        brickwall_layout(n, L, c->plan.first_qubit);
+        c->plan.n = n; c->plan.L = L; c->plan.K = c->K;
+        c->nb = (int)c->blocks.size();
+        c->P = 0;
+        int sms = 152;
+        CUDA_TRY(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device));
+        const long long ncols = (long long)ns << (n - 5);
+        c->tc_ctas_fwd = std::max(1, std::min(sms, tcb_tiles(ncols, false)));
+        c->tc_ctas_bwd = std::max(1, std::min(sms, tcb_tiles(ncols, true)));
+        c->ovl_chunks = (int)std::max<long long>(1, std::min<long long>(((long long)1 << n) / 4096, (4 * sms + ns - 1) / ns));
+    } else if (c->unfused) {
         brickwall_layout(n, L, c->plan.first_qubit);
         c->plan.n = n; c->plan.L = L; c->plan.K = c->K;
         c->cx_count = unfused_cx_count(n, ns);
@@ -660,7 +811,34 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_res, sizeof(double) * c->res_len));
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_status, sizeof(int)));
 
-    if (c->unfused) {
+    if (c->tensor) {
+        std::vector<DevBlock> db;
+        std::vector<DevBlockGate> dbg;
+        for (const BlockPlan& bp : c->blocks) {
+            db.push_back(DevBlock{bp.a, (int)bp.gates.size(), (int)dbg.size(), 0});
+            for (int k : bp.gates) dbg.push_back(DevBlockGate{k, c->plan.first_qubit[k] - bp.a});
+        }
+        const size_t sbytes = 16 * dim * ns;
+        size_t free_b = 0, total_b = 0;
+        CUDA_TRY(c, cudaMemGetInfo(&free_b, &total_b));
+        if ((double)sbytes * c->nb > 0.85 * (double)free_b)
+            return fail(c, HVP_ENOMEM, fmt("HVP_TENSOR: %d block-boundary state sets of %zu bytes do not fit in 85%% of "
+                                          "the free device memory", c->nb, sbytes));
+        if ((rc = dalloc(c, (void**)&c->d_blocks, sizeof(DevBlock) * db.size()))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_bgates, sizeof(DevBlockGate) * dbg.size()))) return rc;
+        CUDA_TRY(c, cudaMemcpy(c->d_blocks, db.data(), sizeof(DevBlock) * db.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_bgates, dbg.data(), sizeof(DevBlockGate) * dbg.size(), cudaMemcpyHostToDevice));
+        if ((rc = dalloc(c, (void**)&c->d_mats64, sizeof(Mats64) * (size_t)c->K))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_ops, sizeof(uint32_t) * kOpWords * (size_t)c->nb))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_rec, sizeof(double) * 16384 * (size_t)c->nb * c->tc_ctas_bwd))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_psum, sizeof(double) * 16384 * (size_t)c->nb))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_Ew, sizeof(double2) * 16 * (size_t)c->K))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_DEw, sizeof(double2) * 16 * (size_t)c->K))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_ovl, sizeof(double) * 4 * (size_t)ns * c->ovl_chunks))) return rc;
+        c->tstate.assign(c->nb, nullptr);
+        for (int j = 0; j < c->nb; ++j)
+            if ((rc = dalloc(c, &c->tstate[j], sbytes))) return rc;
+    } else if (c->unfused) {
         if ((rc = dalloc(c, &c->d_x, state_elt(c) * dim * ns))) return rc;
     } else {
         std::vector<DevPass> dp;
@@ -741,6 +919,8 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     // Input states.
     double* tmp = nullptr;
     const size_t tmp_bytes = sizeof(double) * std::max((size_t)ns * n * 4, (cfg->flags & HVP_PHI_GIVEN) ? dim * ns * 2 : 0);
+    if (c->bytes + tmp_bytes > device_alloc_cap())
+        return fail(c, HVP_ENOMEM, "temporary input buffer exceeds the cap HVP_DEVICE_ALLOC_CAP_MB");
     if (cudaMalloc((void**)&tmp, tmp_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, HVP_ENOMEM, "temporary input buffer");
@@ -751,7 +931,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     else CUDA_TRY(c, launch_psi1q_convert(tmp, (float2*)c->d_psi1q, (size_t)ns * n * 2, c->stream));
     if (cfg->flags & HVP_PHI_GIVEN) {
         std::vector<int> pos(n);
-        if (c->unfused) {
+        if (c->unfused || c->tensor) {
             for (int q = 0; q < n; ++q) pos[q] = n - 1 - q;
         } else {
             pos = c->plan.passes[c->P - 1].pos_in;
@@ -1104,6 +1284,8 @@ int hvp_get(hvp_ctx* c, int what, double* out) {
         case HVP_OUT_HVP_R: off = c->off_hr(); len = n32; break;
         case HVP_OUT_LOSS: off = 0; len = 1; break;
         case HVP_OUT_ENV:
+            if (c->tensor)
+                return fail(c, HVP_EINVAL, "HVP_OUT_ENV: the HVP_TENSOR schedule sums environments over samples");
             CUDA_TRY(c, cudaMemcpyAsync(out, c->d_env, sizeof(double) * 64 * c->K * ns, cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));
             return HVP_OK;
@@ -1121,6 +1303,18 @@ int hvp_plan_info(const hvp_ctx* c, long long info[10]) {
         return HVP_OK;
     }
     info[0] = c->K;
+    if (c->tensor) {
+        info[1] = c->nb;
+        info[2] = kBlockQ;
+        info[3] = 0;
+        info[4] = c->launches_per_call[1];
+        info[5] = (long long)(c->bytes >> 20);
+        info[6] = 0;
+        info[7] = c->tc_ctas_bwd;
+        info[8] = 256;
+        info[9] = 0;
+        return HVP_OK;
+    }
     info[1] = c->unfused ? c->K : c->P;
     info[2] = c->w;
     info[3] = c->cache ? 0 : c->stride;
@@ -1143,10 +1337,15 @@ int hvp_batch_wait_test(hvp_ctx* c, int dep_bias, long long spin_limit) {
 
 int hvp_cache_wait_test(hvp_ctx* c, int extra_bytes, long long spin_limit) {
     if (!c) return fail(nullptr, HVP_EINVAL, "hvp_cache_wait_test: ctx is NULL");
-    if (!c->cache) return fail(c, HVP_EINVAL, "hvp_cache_wait_test: the context does not run the forward cache");
+    if (!c->cache && !c->tensor)
+        return fail(c, HVP_EINVAL, "hvp_cache_wait_test: the context does not run the forward cache");
     if ((extra_bytes != 0 && extra_bytes != 16) || spin_limit < 0 || spin_limit > 0x7fffffffll)
         return fail(c, HVP_EINVAL, "hvp_cache_wait_test: extra_bytes must be 0 or 16, spin_limit in [0, 2^31)");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (c->tensor) {
+        c->tc_wait_limit = extra_bytes ? (unsigned)std::max<long long>(1, spin_limit) : 0u;
+        c->tc_barrier_extra = extra_bytes ? 1u : 0u;
+    }
     c->copy_extra_bytes = (unsigned)extra_bytes;
     c->copy_wait_limit = (unsigned)spin_limit;
     for (auto& g : c->gexec)   // the kernel arguments are baked into the captured graphs

@@ -494,6 +494,10 @@ namespace {
 int balloc(BatchImpl* b, void** p, size_t bytes, std::string& err) {
     *p = nullptr;
     if (!bytes) return HVP_OK;
+    if (b->bytes + bytes > device_alloc_cap()) {
+        err = "device allocation of " + std::to_string(bytes) + " bytes exceeds the cap HVP_DEVICE_ALLOC_CAP_MB";
+        return HVP_ENOMEM;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();

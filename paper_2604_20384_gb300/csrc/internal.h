@@ -7,7 +7,21 @@
 #include <cstdint>
 #include <vector>
 
+#include <cstdlib>
+
 namespace hvp {
+
+// Failure injection on the host: with HVP_DEVICE_ALLOC_CAP_MB set, a context
+// (or batch) whose device allocations would exceed that many MiB fails with
+// HVP_ENOMEM exactly as if cudaMalloc had failed (tests of the error path).
+inline size_t device_alloc_cap() {
+    const char* v = std::getenv("HVP_DEVICE_ALLOC_CAP_MB");
+    if (!v || !*v) return ~(size_t)0;
+    char* end = nullptr;
+    const unsigned long long mb = std::strtoull(v, &end, 10);
+    if (end == v) return ~(size_t)0;
+    return (size_t)mb << 20;
+}
 
 constexpr int kMaxN = 30;            // qubits
 constexpr int kMaxSamples = 65535;   // samples of one context (grid rows of the window passes)
@@ -31,6 +45,28 @@ struct Plan {
     std::vector<int> first_qubit;   // gate k acts on (first_qubit[k], first_qubit[k] + 1)
     std::vector<PassPlan> passes;
     std::vector<int> pass_of_gate;
+};
+
+// One fused block of the tensor-core schedule: gates acting inside the
+// kBlockQ qubits [a, a + kBlockQ), in circuit order.
+constexpr int kBlockQ = 5;
+struct BlockPlan {
+    int a;
+    std::vector<int> gates;
+};
+int make_block_plan(int n, int L, std::vector<BlockPlan>& blocks);
+
+// Device form of a block plan: block j owns the gate records
+// [gate_off, gate_off + n_gates) in circuit order.
+struct DevBlock {
+    int a;          // first qubit of the block
+    int n_gates;
+    int gate_off;
+    int pad;
+};
+struct DevBlockGate {
+    int k;          // gate index
+    int u;          // qubit offset of the gate inside the block (0 .. kBlockQ - 2)
 };
 
 int num_gates(int n, int L);
@@ -67,6 +103,57 @@ struct DevGate {
 
 void build_dev_passes(const Plan& plan, std::vector<DevPass>& dp, std::vector<DevGate>& dg);
 
+// ------------------------------------------- fused-block (tensor-core) passes
+
+// One launch applies one block to every amplitude of every sample. Modes:
+// forward, X -> [[B, 0], [dB, B]] X; backward, C -> [[B^dag, 0], [dB^dag,
+// B^dag]] C with the block environment of the co-states after the update and
+// the forward states at the block's input accumulated into rec.
+enum TcbMode : int {
+    TCB_GEN = 1,       // forward states of the block's input generated (product states)
+    TCB_LOAD_PHI = 2,  // backward: co-states start as (w1 phi, w2 phi)
+    TCB_NO_STORE = 4,  // backward: the updated co-states are not stored (first block)
+    TCB_NO_TANGENT = 8,  // the tangent components are zero and stay zero (no GEMM on them)
+};
+
+// Operator record of one block (kOpWords 32-bit words). For direction d (0
+// forward [[B, 0], [dB, B]], 1 backward [[B^dag, 0], [dB^dag, B^dag]]) and
+// half h (0: the operator's columns acting on the state components, 1: on the
+// tangent components), slice i = 0, 1, 2: 128 rows x 32 words, each word two
+// bf16 integers in [-256, 256] (K elements 2w in the low half, 2w + 1 in the
+// high half; K = 2 b + (re, im)); then the row scales [d][h][128] as floats.
+// Row m of half h is scale * (s_0 + s_1 / 256 + s_2 / 65536) exactly up to
+// 2^-25 of the row's largest entry.
+constexpr int kOpSliceWords = 128 * 32;
+constexpr int kOpScaleOff = 2 * 2 * 3 * kOpSliceWords;
+constexpr int kOpWords = kOpScaleOff + 2 * 2 * 128;
+
+struct TcbArgs {
+    const uint32_t* ops;     // this block's operator record (kOpWords words)
+    const float4* xin;       // forward: states at the block's input; backward: co-states
+    float4* xout;            // forward: states at the block's output; backward: co-states (in place)
+    const float4* psi;       // backward: forward states at the block's input
+    const float2* phi;       // backward with TCB_LOAD_PHI: reference states (standard order)
+    const double2* w1;       // with TCB_LOAD_PHI: per-sample weights (T_s), or null for 1
+    const double2* w2;       // per-sample weights (Omega_s), or null for 0
+    const float2* psi1q;     // N_s x n x 2 single-qubit factors (TCB_GEN)
+    double* rec;             // backward: FP64 environment records of this block, [CTA][128][128]
+    int* status;             // bit 2: a bounded wait gave up
+    long long ncols;         // N_s * 2^(n - 5)
+    int n, a, mode;
+    unsigned wait_limit;     // polls before a wait gives up (0: the default)
+    unsigned barrier_extra;  // test of the bounded waits: arrivals the tile barriers expect beyond the
+                             // MMAs' commit (0 in normal use)
+};
+cudaError_t launch_tcb(const TcbArgs& a, bool bwd, int ctas, cudaStream_t st);
+cudaError_t tcb_set_smem_limits();
+int tcb_tiles(long long ncols, bool bwd);
+cudaError_t launch_block_prep(const DevBlock* blocks, const DevBlockGate* bg, int nb, const double2* G,
+                              const double2* V, uint32_t* ops, int* status, cudaStream_t st);
+cudaError_t launch_overlaps(const float4* x, const float2* phi, double* partial, double2* T, double2* Om, int n,
+                            int ns, int chunks, cudaStream_t st);
+cudaError_t launch_extract_psi(const float4* x, float2* out, size_t count, cudaStream_t st);
+
 // Swizzle of shared-memory element indices (16-byte elements): conflict-free
 // 128-bit accesses when no two neighbouring qubits sit on index bits 0..2.
 __host__ __device__ inline unsigned swz(unsigned l) {
@@ -88,6 +175,9 @@ enum PassMode : int {
 // Y = G^-1 V G^-1 (so that dpsi^[k-1] = G^-1 dpsi^[k] - Y psi^[k]).
 struct Mats32 { float2 G[16], Ginv[16], Gh[16], V[16], Vh[16], Y[16]; };
 struct Mats64 { double2 G[16], Ginv[16], Gh[16], V[16], Vh[16], Y[16]; };
+cudaError_t launch_block_post(const DevBlock* blocks, const DevBlockGate* bg, int nb, const double* rec, int cx,
+                              double* psum, const Mats64* mats, double2* Ew, double2* DEw, int tangent,
+                              cudaStream_t st);
 
 struct TiledArgs {
     const DevPass* pass;
@@ -161,6 +251,11 @@ struct PostArgs {
     int frobenius;          // 1: derivatives of C_F = 1 - mean Re T instead of C
 };
 cudaError_t launch_post(const PostArgs& p, cudaStream_t st);
+// grad / HVP (Euclidean and App. F) and the loss from sample-summed weighted
+// environments (fused-block schedule).
+cudaError_t launch_post_weighted(const double2* Ew, const double2* DEw, const double2* G, const double2* V,
+                                 const double2* T, double2* ge, double2* he, double2* gr, double2* hr, double* loss,
+                                 int K, int ns, int tangent, int frob, cudaStream_t st);
 cudaError_t launch_prep(const double2* G, const double2* V, void* mats, bool dbl, int K, int* status,
                         cudaStream_t st);
 cudaError_t launch_psi1q_convert(const double* in, float2* out, size_t count, cudaStream_t st);

@@ -1,6 +1,7 @@
 // hvp_hvp_noalloc: loss, gradient and HVP for callers that must not allocate
-// device memory (a framework whose allocator owns the device pool, a replay
-// harness with a frozen memory plan, a process under a hard memory budget).
+// device memory (a framework whose allocator owns the device pool, a process
+// under a hard device-memory budget). The call is synchronous: it uploads its
+// tables from host memory and waits for its stream before returning.
 //
 // It runs the existing single-window schedule (one tile of 2^n amplitudes per
 // sample, n <= 12): FP64 gate preparation, one window pass that goes forward
@@ -121,8 +122,10 @@ extern "C" int hvp_hvp_noalloc(int n, int n_layers, int n_samples, const double*
     std::vector<DevPass> dp;
     std::vector<DevGate> dg;
     build_dev_passes(plan, dp, dg);
+    // phi (given in the standard layout) goes into the layout in which the
+    // single pass reads its co-states
     int pos[32];
-    for (int q = 0; q < n; ++q) pos[q] = n - 1 - q;
+    for (int q = 0; q < n; ++q) pos[q] = plan.passes[0].pos_in[q];
 
     DevPass* d_pass = reinterpret_cast<DevPass*>(base + lay.pass);
     DevGate* d_gates = reinterpret_cast<DevGate*>(base + lay.gates);

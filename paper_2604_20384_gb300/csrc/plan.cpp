@@ -499,6 +499,42 @@ void build_dev_passes(const Plan& plan, std::vector<DevPass>& dps, std::vector<D
     }
 }
 
+// Fused-block plan of the tensor-core schedule: the gate sequence split into
+// blocks of kBlockQ neighbouring qubits [a, a + kBlockQ); a block holds every
+// gate inside its qubits whose predecessors lie in earlier blocks or earlier
+// in the same block, in circuit order. The beam search of the window planner
+// (windows of kBlockQ qubits, no overlap condition between consecutive
+// windows) minimises the number of blocks, i.e. of dense 2^kBlockQ x
+// 2^kBlockQ products per amplitude.
+int make_block_plan(int n, int L, std::vector<BlockPlan>& blocks) {
+    blocks.clear();
+    if (n < kBlockQ || n > kMaxN || L < 1) return HVP_EINVAL;
+    std::vector<int> fq;
+    brickwall_layout(n, L, fq);
+    const int K = (int)fq.size();
+    std::vector<int> last(n, -1), p1(K), p2(K);
+    for (int k = 0; k < K; ++k) {
+        p1[k] = last[fq[k]];
+        p2[k] = last[fq[k] + 1];
+        last[fq[k]] = last[fq[k] + 1] = k;
+    }
+    std::vector<std::pair<Window, std::vector<int>>> bw;
+    if (n == kBlockQ) {
+        std::vector<int> all(K);
+        for (int k = 0; k < K; ++k) all[k] = k;
+        bw.emplace_back(Window{0, n - 1}, all);
+    } else if (!beam_plan(n, kBlockQ, 0, fq, p1, p2, bw)) {
+        return HVP_EINVAL;
+    }
+    int covered = 0;
+    for (auto& pr : bw) {
+        if (pr.second.empty()) continue;
+        covered += (int)pr.second.size();
+        blocks.push_back(BlockPlan{pr.first.lo, std::move(pr.second)});
+    }
+    return covered == K ? HVP_OK : HVP_EINVAL;
+}
+
 }  // namespace hvp
 
 extern "C" int hvp_num_gates(int n, int n_layers) { return hvp::num_gates(n, n_layers); }
@@ -510,4 +546,18 @@ extern "C" int hvp_plan_brickwall(int n, int n_layers, int window, int low_bits,
     if (pass_of_gate)
         for (int k = 0; k < plan.K; ++k) pass_of_gate[k] = plan.pass_of_gate[k];
     return (int)plan.passes.size();
+}
+
+// Block plan of the tensor-core schedule for tests: block_of_gate[k] = block
+// of gate k, block_qubit[j] = first qubit of block j (arrays of K entries).
+extern "C" int hvp_plan_blocks(int n, int n_layers, int* block_of_gate, int* block_qubit) {
+    std::vector<hvp::BlockPlan> blocks;
+    int rc = hvp::make_block_plan(n, n_layers, blocks);
+    if (rc != HVP_OK) return rc;
+    for (size_t j = 0; j < blocks.size(); ++j) {
+        if (block_qubit) block_qubit[j] = blocks[j].a;
+        if (block_of_gate)
+            for (int k : blocks[j].gates) block_of_gate[k] = (int)j;
+    }
+    return (int)blocks.size();
 }

@@ -140,6 +140,37 @@ __global__ void overlaps_kernel(const double* __restrict__ env, const double2* _
     }
 }
 
+// Stores gate k's entry e (16 threads per gate) of the Euclidean gradient g
+// and HVP h, then their projections to the tangent space of U(4) at G_k
+// (App. F): grad_R = P_G(g), H_R = P_G(h - V g^dag G / 2 - G g^dag V / 2),
+// with P_G(X) = X / 2 - G X^dag G / 2.
+__device__ void finish_gate(int k, int e, double2 g, double2 h, const double2* __restrict__ G,
+                            const double2* __restrict__ V, double2* ge, double2* he, double2* gr, double2* hr,
+                            int tangent) {
+    __shared__ double2 sG[16], sV[16], sg[16], sX[16];
+    sG[e] = G[k * 16 + e];
+    sV[e] = tangent ? V[k * 16 + e] : make_double2(0.0, 0.0);
+    sg[e] = g;
+    ge[k * 16 + e] = g;
+    if (tangent) he[k * 16 + e] = h;
+    __syncthreads();
+    const int r = e >> 2, c = e & 3;
+    // A B^dag C entry (r, c) = sum_a sum_b A[r][a] conj(B[b][a]) C[b][c].
+    auto abdc = [&](const double2* A, const double2* B, const double2* Cm) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) acc = dadd(acc, dmul(dmul(A[r * 4 + a], dconj(B[b * 4 + a])), Cm[b * 4 + c]));
+        return acc;
+    };
+    gr[k * 16 + e] = dsub(dscale(g, 0.5), dscale(abdc(sG, sg, sG), 0.5));
+    if (tangent) {
+        const double2 x = dsub(dsub(h, dscale(abdc(sV, sg, sG), 0.5)), dscale(abdc(sG, sg, sV), 0.5));
+        sX[e] = x;
+        __syncthreads();
+        hr[k * 16 + e] = dsub(dscale(x, 0.5), dscale(abdc(sG, sX, sG), 0.5));
+    }
+}
+
 // Gradient and HVP of C = 1 - (1/N_s) sum |T_s|^2 per gate, then the tangent-space
 // projections of App. F. Block k handles gate k with 16 threads (one per entry).
 __global__ void grad_kernel(const double* __restrict__ env, const double2* __restrict__ G,
@@ -147,7 +178,6 @@ __global__ void grad_kernel(const double* __restrict__ env, const double2* __res
                             const double2* __restrict__ Om, double2* ge, double2* he, double2* gr, double2* hr,
                             int K, int ns, int tangent, int frob) {
     const int k = blockIdx.x, e = threadIdx.x;
-    __shared__ double2 sG[16], sV[16], sg[16], sX[16];
     double2 g = make_double2(0.0, 0.0), h = make_double2(0.0, 0.0);
     for (int s = 0; s < ns; ++s) {
         const double2* Es = reinterpret_cast<const double2*>(env + ((size_t)s * K + k) * 64);
@@ -164,31 +194,20 @@ __global__ void grad_kernel(const double* __restrict__ env, const double2* __res
         }
     }
     const double scale = (frob ? -1.0 : -2.0) / ns;
-    g = dscale(g, scale);
-    h = dscale(h, scale);
-    sG[e] = G[k * 16 + e];
-    sV[e] = tangent ? V[k * 16 + e] : make_double2(0.0, 0.0);
-    sg[e] = g;
-    ge[k * 16 + e] = g;
-    if (tangent) he[k * 16 + e] = h;
-    __syncthreads();
-    const int r = e >> 2, c = e & 3;
-    // A B^dag C entry (r, c) = sum_a sum_b A[r][a] conj(B[b][a]) C[b][c].
-    auto abdc = [&](const double2* A, const double2* B, const double2* Cm) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 4; ++b) acc = dadd(acc, dmul(dmul(A[r * 4 + a], dconj(B[b * 4 + a])), Cm[b * 4 + c]));
-        return acc;
-    };
-    // grad_R = P_G(grad) = grad/2 - G grad^dag G/2.
-    gr[k * 16 + e] = dsub(dscale(g, 0.5), dscale(abdc(sG, sg, sG), 0.5));
-    if (tangent) {
-        // X = H - V grad^dag G/2 - G grad^dag V/2;  H_R = P_G(X).
-        const double2 x = dsub(dsub(h, dscale(abdc(sV, sg, sG), 0.5)), dscale(abdc(sG, sg, sV), 0.5));
-        sX[e] = x;
-        __syncthreads();
-        hr[k * 16 + e] = dsub(dscale(x, 0.5), dscale(abdc(sG, sX, sG), 0.5));
-    }
+    finish_gate(k, e, dscale(g, scale), dscale(h, scale), G, V, ge, he, gr, hr, tangent);
+}
+
+// The same from sample-summed weighted environments (the fused-block
+// schedule): Ew = sum_s conj(T_s) E_s and DEw = sum_s (conj(Omega_s) E_s +
+// conj(T_s) DE_s) (with weights 1 and 0 for the Frobenius cost), so
+// grad = scale conj(Ew) and H[V] = scale conj(DEw).
+__global__ void weighted_grad_kernel(const double2* __restrict__ Ew, const double2* __restrict__ DEw,
+                                     const double2* __restrict__ G, const double2* __restrict__ V, double2* ge,
+                                     double2* he, double2* gr, double2* hr, int K, double scale, int tangent) {
+    const int k = blockIdx.x, e = threadIdx.x;
+    const double2 g = dscale(dconj(Ew[k * 16 + e]), scale);
+    const double2 h = tangent ? dscale(dconj(DEw[k * 16 + e]), scale) : make_double2(0.0, 0.0);
+    finish_gate(k, e, g, h, G, V, ge, he, gr, hr, tangent);
 }
 
 __global__ void loss_kernel(const double2* __restrict__ T, double* loss, int ns, int frob) {
@@ -238,6 +257,15 @@ cudaError_t launch_post(const PostArgs& p, cudaStream_t st) {
     grad_kernel<<<p.K, 16, 0, st>>>(p.env, p.G, p.V, p.T, p.Omega, p.grad_e, p.hvp_e, p.grad_r, p.hvp_r, p.K,
                                      p.n_samples, p.tangent, p.frobenius);
     loss_kernel<<<1, 256, 0, st>>>(p.T, p.loss, p.n_samples, p.frobenius);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_post_weighted(const double2* Ew, const double2* DEw, const double2* G, const double2* V,
+                                 const double2* T, double2* ge, double2* he, double2* gr, double2* hr, double* loss,
+                                 int K, int ns, int tangent, int frob, cudaStream_t st) {
+    const double scale = (frob ? -1.0 : -2.0) / ns;
+    weighted_grad_kernel<<<K, 16, 0, st>>>(Ew, DEw, G, V, ge, he, gr, hr, K, scale, tangent);
+    loss_kernel<<<1, 256, 0, st>>>(T, loss, ns, frob);
     return cudaGetLastError();
 }
 

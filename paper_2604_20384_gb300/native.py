@@ -19,9 +19,9 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hvp.h")
 HVP_OK, HVP_EINVAL, HVP_ENOMEM, HVP_ECUDA, HVP_ETIMEOUT, HVP_ENONFINITE = 0, -1, -2, -3, -4, -5
 HVP_C64, HVP_C128 = 0, 1
 HVP_RIEMANNIAN, HVP_PHI_GIVEN, HVP_UNFUSED, HVP_NO_GRAPH, HVP_AUTOTUNE, HVP_FROBENIUS = 1, 2, 4, 8, 16, 32
-HVP_RECOMPUTE, HVP_MULTI_DIR = 64, 128
+HVP_RECOMPUTE, HVP_MULTI_DIR, HVP_TENSOR = 64, 128, 256
 KINDS = {0: "prep", 1: "pass_fwd", 2: "pass_turnaround", 3: "pass_bwd", 4: "gate_init", 5: "gate_fwd",
-         6: "gate_load_phi", 7: "gate_bwd", 8: "post"}
+         6: "gate_load_phi", 7: "gate_bwd", 8: "post", 9: "block_fwd", 10: "block_bwd"}
 OUT = dict(T=1, Omega=2, grad_e=3, hvp_e=4, grad_r=5, hvp_r=6, loss=7, env=8)
 ERRORS = {HVP_EINVAL: "EINVAL", HVP_ENOMEM: "ENOMEM", HVP_ECUDA: "ECUDA", HVP_ETIMEOUT: "ETIMEOUT",
           HVP_ENONFINITE: "ENONFINITE"}
@@ -78,6 +78,9 @@ def load() -> ctypes.CDLL:
     lib.hvp_plan_info.restype = ctypes.c_int
     lib.hvp_plan_brickwall.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int)]
     lib.hvp_plan_brickwall.restype = ctypes.c_int
+    lib.hvp_plan_blocks.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]
+    lib.hvp_plan_blocks.restype = ctypes.c_int
     lib.hvp_profile.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                 ctypes.POINTER(ctypes.c_int), _dp, _dp]
     lib.hvp_profile.restype = ctypes.c_int
@@ -116,14 +119,28 @@ def plan_brickwall(n: int, n_layers: int, window: int = 12, low_bits: int = 4):
     return P, np.array(arr[:K], dtype=np.int64)
 
 
+def plan_blocks(n: int, n_layers: int):
+    """(block of every gate, first qubit of every block) of the fused-block
+    plan of the HVP_TENSOR schedule."""
+    lib = load()
+    K = lib.hvp_num_gates(n, n_layers)
+    bog = (ctypes.c_int * max(K, 1))()
+    bq = (ctypes.c_int * max(K, 1))()
+    nb = lib.hvp_plan_blocks(n, n_layers, bog, bq)
+    if nb < 0:
+        raise HVPError(nb, "hvp_plan_blocks failed")
+    return np.array(bog[:K], dtype=np.int64), np.array(bq[:nb], dtype=np.int64)
+
+
 def hvp_noalloc(n: int, n_layers: int, n_samples: int, psi1q_ptr: int, phi_ptr: int, G_ptr: int,
                 V_ptr: int | None, loss_ptr: int | None, grad_ptr: int | None, hvp_ptr: int | None,
                 stream: int | None = None) -> None:
     """Loss, gradient and HVP on device pointers without any device allocation
-    (hvp_hvp_noalloc): for callers whose memory is owned by someone else, e.g.
-    a framework allocator holding the whole device pool or a frozen memory
-    plan. Work space is a fixed 16 MiB static device array shared by all calls
-    on a device, so calls must not overlap on the GPU."""
+    (hvp_hvp_noalloc): for callers whose device memory is owned by someone
+    else, e.g. a framework allocator holding the whole device pool, or that
+    run under a strict device-memory budget. Work space is a fixed 16 MiB
+    static device array shared by all calls on a device, so calls must not
+    overlap on the GPU. The call is synchronous (it waits for its stream)."""
     lib = load()
     rc = lib.hvp_hvp_noalloc(n, n_layers, n_samples, psi1q_ptr, phi_ptr, G_ptr, V_ptr, loss_ptr, grad_ptr,
                              hvp_ptr, stream)
@@ -153,7 +170,7 @@ class Context:
                  riemannian: bool = False, phi_given: bool = False, unfused: bool = False,
                  graphs: bool = True, checkpoint_stride: int = 0, window: int = 0, threads: int = 0,
                  variant: int = 0, autotune: bool = False, frobenius: bool = False, recompute: bool = False,
-                 multi_dir: bool = False, device: int = 0, stream: int | None = None):
+                 multi_dir: bool = False, tensor: bool = False, device: int = 0, stream: int | None = None):
         self._lib = load()
         psi1q = np.asarray(psi1q)
         self.n, self.n_layers, self.n_samples = n, n_layers, int(psi1q.shape[0])
@@ -161,7 +178,8 @@ class Context:
         flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
                  | (HVP_UNFUSED if unfused else 0) | (0 if graphs else HVP_NO_GRAPH)
                  | (HVP_AUTOTUNE if autotune else 0) | (HVP_FROBENIUS if frobenius else 0)
-                 | (HVP_RECOMPUTE if recompute else 0) | (HVP_MULTI_DIR if multi_dir else 0))
+                 | (HVP_RECOMPUTE if recompute else 0) | (HVP_MULTI_DIR if multi_dir else 0)
+                 | (HVP_TENSOR if tensor else 0))
         cfg = HVPConfig(n, n_layers, self.n_samples, HVP_C128 if precision == "c128" else HVP_C64, flags,
                         checkpoint_stride, window, threads, variant, device, stream)
         self._psi = _f64(psi1q)

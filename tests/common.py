@@ -40,3 +40,45 @@ def grad_at(w, phi, G, threads=None):
 def expm_skew(x):
     w, u = np.linalg.eigh(-1j * x)
     return (u * np.exp(1j * w)[None, :]) @ u.conj().T
+
+
+def _phi_chunk(args):
+    n, L, uref, psi1q = args
+    return oracle.reference_states(n, L, uref, psi1q)
+
+
+def oracle_parallel(w, G=None, V=None):
+    """Oracle on every sample of workload w using the host's cores: reference
+    states in a spawned process pool (chunks of samples), then one evaluation
+    with a thread per core."""
+    import multiprocessing as mp
+    import os
+
+    cores = os.cpu_count() or 1
+    step = max(1, -(-w.n_samples // cores))
+    chunks = [w.psi1q[i:i + step] for i in range(0, w.n_samples, step)]
+    if len(chunks) > 1:
+        with mp.get_context("spawn").Pool(min(cores, len(chunks))) as pool:
+            parts = pool.map(_phi_chunk, [(w.n, w.n_layers, w.Uref, c) for c in chunks])
+        phi = np.concatenate(parts)
+    else:
+        phi = oracle.reference_states(w.n, w.n_layers, w.Uref, w.psi1q)
+    o = oracle.evaluate(w.n, w.n_layers, w.G if G is None else G, w.V if V is None else V, w.psi1q, phi,
+                        threads=cores, ckpt_stride=max(1, int(round(w.K ** 0.5))))
+    return phi, o
+
+
+_HEADLINE = {}
+
+
+def headline_oracle():
+    """The benchmark workload (n = 20, L = 16, N_s = 64, seed 0) and the oracle
+    on all of its samples: reference states in a spawned process pool (chunks
+    of samples), then one oracle evaluation with a thread per host core and
+    forward checkpoints every 12 gates. Cached for the test session (about a
+    minute on 16 cores)."""
+    if "o" not in _HEADLINE:
+        w = make_workload(20, 16, 64, seed=0)
+        phi, o = oracle_parallel(w)
+        _HEADLINE.update(w=w, phi=phi, o=o)
+    return _HEADLINE["w"], _HEADLINE["phi"], _HEADLINE["o"]

@@ -70,6 +70,33 @@ def test_plan_pass_counts_of_benchmark_shapes():
     assert native.plan_brickwall(12, 8, 12, 4)[0] == 1
 
 
+@pytest.mark.parametrize("n,L", [(20, 16), (5, 7), (6, 3), (12, 8), (26, 24), (13, 11), (30, 5), (9, 1)])
+def test_block_plan_covers_gates_in_circuit_order(n, L):
+    # Fused-block plan of the tensor-core schedule: every gate in exactly one
+    # block, both of its qubits inside the block's five qubits [a, a + 5), and
+    # no gate in an earlier block than a gate it depends on (within a block the
+    # gates run in circuit order, which respects every dependency).
+    bog, bq = native.plan_blocks(n, L)
+    K = num_gates(n, L)
+    fq = [i for layer in range(1, L + 1) for i in range((layer - 1) % 2, n - 1, 2)]
+    assert len(bog) == K and bog.min() == 0 and bog.max() == len(bq) - 1
+    assert np.all((bq >= 0) & (bq + 5 <= n))
+    for k in range(K):
+        a = bq[bog[k]]
+        assert a <= fq[k] and fq[k] + 1 <= a + 4
+    for g, ds in enumerate(_deps(n, L)):
+        for d in ds:
+            assert bog[d] <= bog[g]
+
+
+def test_block_plan_of_benchmark_shape():
+    # n = 20, L = 16: 152 gates in 26 blocks of five qubits (about six gates
+    # per dense 32 x 32 block); fewer than five qubits cannot form a block.
+    bog, bq = native.plan_blocks(20, 16)
+    assert len(bq) == 26
+    assert native.load().hvp_plan_blocks(4, 3, None, None) == -1
+
+
 def test_plan_rejects_bad_arguments():
     lib = native.load()
     assert lib.hvp_plan_brickwall(1, 3, 12, 4, None) < 0

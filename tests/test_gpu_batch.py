@@ -3,7 +3,7 @@ oracle and against single-circuit contexts."""
 import numpy as np
 import pytest
 
-from common import rel
+from common import oracle_parallel, rel
 from oracle import oracle
 from paper_2604_20384_gb300 import native
 from paper_2604_20384_gb300.inputs import make_workload, uneven_batch_shapes
@@ -76,7 +76,7 @@ def test_expired_chain_wait_is_reported_and_context_stays_usable():
         assert rel(hvps[i], o["hvp"]) < TOL, (i, rel(hvps[i], o["hvp"]))
 
 
-def test_full_uneven_batch_matches_single_contexts():
+def test_full_uneven_batch_matches_single_contexts_and_oracle():
     # 64 circuits, n ~ U{8..16}, L ~ U{4..20}, N_s log-uniform in [32, 512]
     shapes = uneven_batch_shapes(64, seed=0)
     ws = [make_workload(n, L, ns, s) for (n, L, ns, s) in shapes]
@@ -88,8 +88,14 @@ def test_full_uneven_batch_matches_single_contexts():
     assert np.array_equal(r1[0], r2[0])
     assert all(np.array_equal(a, c) for a, c in zip(r1[2], r2[2]))
     assert np.all((r1[0] >= 0) & (r1[0] <= 1))
-    picks = sorted({int(i) for i in np.random.default_rng(3).choice(64, 6, replace=False)} |
-                   {int(np.argmax([w.n for w in ws])), int(np.argmin([w.n for w in ws]))})
+    # circuits checked against single-circuit contexts and against the FP64
+    # oracle: the largest n, the smallest n, the largest N_s, and five more at
+    # random among those the oracle evaluates in a few seconds on the host
+    cost = [(1 << w.n) * w.n_samples * w.K for w in ws]
+    light = [i for i in range(64) if cost[i] < 5e8]
+    picks = sorted({int(np.argmax([w.n for w in ws])), int(np.argmin([w.n for w in ws])),
+                    int(np.argmax([w.n_samples for w in ws]))} |
+                   {int(i) for i in np.random.default_rng(3).choice(light, 5, replace=False)})
     for i in picks:
         w = ws[i]
         with native.Context(w.n, w.n_layers, w.psi1q, w.Uref) as c:
@@ -97,3 +103,7 @@ def test_full_uneven_batch_matches_single_contexts():
         assert abs((1 - r1[0][i]) - (1 - loss)) <= TOL * (1 - loss) + 1e-13, i
         assert rel(r1[1][i], g) < TOL, (i, w.n)
         assert rel(r1[2][i], h) < TOL, (i, w.n)
+        phi, o = oracle_parallel(w)
+        assert abs((1 - r1[0][i]) - (1 - o["loss"])) <= TOL * (1 - o["loss"]) + 1e-13, i
+        assert rel(r1[1][i], o["grad"]) < TOL, (i, w.n, rel(r1[1][i], o["grad"]))
+        assert rel(r1[2][i], o["hvp"]) < TOL, (i, w.n, rel(r1[2][i], o["hvp"]))

@@ -9,7 +9,7 @@ circuits) and as C absolutely.
 import numpy as np
 import pytest
 
-from common import rel
+from common import headline_oracle, rel
 from oracle import oracle
 from paper_2604_20384_gb300 import native
 from paper_2604_20384_gb300.inputs import make_workload, random_direction
@@ -236,9 +236,11 @@ def test_maximum_size_solution_point_and_directional_derivative():
 def test_headline_shape_sampled_against_oracle(threads, window, recompute):
     # n = 20, L = 16, N_s = 64 in the benchmark's launch configurations (12-
     # and 11-qubit windows; forward states cached before every gate, 152 GiB,
-    # or recomputed inside each pass); the oracle checks two of the samples
-    # one by one (T_s, Omega_s and every per-sample environment), and the
-    # sample-summed outputs are checked through linearity in the samples.
+    # or recomputed inside each pass); the oracle checks eight of the samples,
+    # spread over the 64, one by one (T_s, Omega_s and every per-sample
+    # environment), and the sample-summed outputs are checked through
+    # linearity in the samples (and against the oracle on all 64 samples in
+    # test_headline_shape_sample_sums_against_oracle_on_all_samples).
     w = make_workload(20, 16, 64, seed=0)
     with native.Context(20, 16, w.psi1q, w.Uref, threads=threads, window=window, recompute=recompute) as ctx:
         info = ctx.plan_info()
@@ -250,10 +252,13 @@ def test_headline_shape_sampled_against_oracle(threads, window, recompute):
         assert r0[0] == loss and np.array_equal(r0[1], grad) and np.array_equal(r0[2], hvp)
         T, Om = ctx.get("T"), ctx.get("Omega")
         E, DE = ctx.get("env")
-    pick = [0, 37]
+    import os
+
+    pick = [0, 9, 18, 27, 37, 46, 55, 63]
     sub = w.psi1q[pick]
     phi = oracle.reference_states(20, 16, w.Uref, sub)
-    o = oracle.evaluate(20, 16, w.G, w.V, sub, phi, threads=2, ckpt_stride=12, want_env=True)
+    o = oracle.evaluate(20, 16, w.G, w.V, sub, phi, threads=min(len(pick), os.cpu_count() or 1), ckpt_stride=12,
+                        want_env=True)
     assert rel(T[pick], o["T"]) < TOL["c64"]
     assert rel(Om[pick], o["Omega"]) < TOL["c64"]
     for i, s in enumerate(pick):
@@ -264,6 +269,15 @@ def test_headline_shape_sampled_against_oracle(threads, window, recompute):
     h = -(2 / 64) * (np.einsum("s,skij->kij", Om, E.conj()) + np.einsum("s,skij->kij", T, DE.conj()))
     assert rel(grad, g) < 1e-9 and rel(hvp, h) < 1e-9
     assert abs(loss - (1 - np.mean(np.abs(T) ** 2))) < 1e-12
+
+
+def test_headline_shape_sample_sums_against_oracle_on_all_samples():
+    # the benchmark workload in its default (autotuned-equivalent) window-pass
+    # configuration: loss, gradient and HVP summed over all 64 samples against
+    # the oracle run on all 64 samples
+    w, phi, o = headline_oracle()
+    with native.Context(20, 16, w.psi1q, w.Uref) as ctx:
+        _check(ctx, w, o, TOL["c64"])
 
 
 @pytest.mark.parametrize("threads", [256, 128])
