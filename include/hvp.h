@@ -90,6 +90,14 @@ extern "C" {
                              block environments sum over samples. Needs
                              complex64 and n >= 5; per-sample environments
                              (HVP_OUT_ENV) are not formed                     */
+#define HVP_TRANSLATION 512 /* translation-invariant layers (App. E, Alg. 3):
+                             every gate of layer l is one layer gate G_l; G and
+                             V hold n_layers*32 doubles (one 4x4 block per
+                             layer), and grad and hvp (Euclidean and
+                             Riemannian) are the derivatives with respect to
+                             the layer gates, the sums of the per-gate blocks
+                             over each layer, formed in FP64 on the device.
+                             Not with HVP_MULTI_DIR; HVP_OUT_ENV stays per gate */
 
 typedef struct hvp_ctx hvp_ctx;
 

@@ -124,6 +124,13 @@ struct hvp_ctx {
     double2* d_DEw = nullptr;       // per gate: sum_s conj(Omega_s) E_s + conj(T_s) DE_s
     double* d_ovl = nullptr;        // overlap partial sums
     unsigned tc_wait_limit = 0, tc_barrier_extra = 0;   // hvp_cache_wait_test on a tensor context
+    // translation-invariant layers (HVP_TRANSLATION, App. E): the caller's gates
+    // and directions are per layer, expanded to every gate on the device, and the
+    // per-gate derivative blocks are summed per layer on the device
+    bool ti = false;
+    double2* d_GL = nullptr;
+    double2* d_VL = nullptr;
+    int* d_layer_first = nullptr;   // first gate of each layer, n_layers + 1 entries
 
     size_t off_T() const { return 2; }
     size_t off_Om() const { return 2 + 2 * (size_t)cfg.n_samples; }
@@ -131,6 +138,16 @@ struct hvp_ctx {
     size_t off_he() const { return off_ge() + 32 * (size_t)K; }
     size_t off_gr() const { return off_he() + 32 * (size_t)K; }
     size_t off_hr() const { return off_gr() + 32 * (size_t)K; }
+    size_t off_layer() const { return off_hr() + 32 * (size_t)K; }   // [ge, he, gr, hr][n_layers][16] complex
+    // the caller's view: 4x4 blocks per call (layers with HVP_TRANSLATION, else gates)
+    size_t n_user() const { return ti ? (size_t)cfg.n_layers : (size_t)K; }
+    // offsets of the caller's outputs: 0 Euclidean gradient, 1 Euclidean HVP, 2 and 3 Riemannian
+    size_t uoff(int i) const {
+        if (ti) return off_layer() + (size_t)i * 32 * cfg.n_layers;
+        return off_ge() + (size_t)i * 32 * K;
+    }
+    double2* in_G() const { return ti ? d_GL : d_G; }
+    double2* in_V() const { return ti ? d_VL : d_V; }
 };
 
 namespace {
@@ -517,7 +534,17 @@ int enqueue_tensor(hvp_ctx* c, bool tan) {
 int enqueue_all(hvp_ctx* c, bool tan) {
     int L = 0, rc;
     CUDA_TRY(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
-    if (c->tensor) return enqueue_tensor(c, tan);
+    if (c->ti)
+        CUDA_TRY(c, launch_expand_layers(c->d_GL, tan ? c->d_VL : nullptr, c->d_G, c->d_V, c->d_layer_first,
+                                         c->cfg.n_layers, c->stream));
+    if (c->tensor) {
+        if ((rc = enqueue_tensor(c, tan))) return rc;
+        if (c->ti)
+            CUDA_TRY(c, launch_contract_layers(reinterpret_cast<const double2*>(c->d_res + c->off_ge()),
+                                               reinterpret_cast<double2*>(c->d_res + c->off_layer()),
+                                               c->d_layer_first, c->cfg.n_layers, c->K, c->stream));
+        return HVP_OK;
+    }
     CUDA_TRY(c, launch_prep(c->d_G, tan ? c->d_V : nullptr, c->d_mats, c->dbl, c->K, c->d_status, c->stream));
     if ((rc = prof_mark(c, HVP_K_PREP, 0.0, 0.0))) return rc;
     ++L;
@@ -543,8 +570,12 @@ int enqueue_all(hvp_ctx* c, bool tan) {
     p.tangent = tan ? 1 : 0;
     p.frobenius = (c->cfg.flags & HVP_FROBENIUS) ? 1 : 0;
     CUDA_TRY(c, launch_post(p, c->stream));
+    if (c->ti)
+        CUDA_TRY(c, launch_contract_layers(reinterpret_cast<const double2*>(c->d_res + c->off_ge()),
+                                           reinterpret_cast<double2*>(c->d_res + c->off_layer()),
+                                           c->d_layer_first, c->cfg.n_layers, c->K, c->stream));
     if ((rc = prof_mark(c, HVP_K_POST, 0.0, 0.0))) return rc;
-    L += 4;
+    L += 4 + (c->ti ? 2 : 0);
     c->launches_per_call[tan ? 1 : 0] = L;
     return HVP_OK;
 }
@@ -659,8 +690,10 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if (cfg->precision != HVP_C64 && cfg->precision != HVP_C128) return fail(c, HVP_EINVAL, "unknown precision");
     if (cfg->flags &
         ~(HVP_RIEMANNIAN | HVP_PHI_GIVEN | HVP_UNFUSED | HVP_NO_GRAPH | HVP_AUTOTUNE | HVP_FROBENIUS | HVP_RECOMPUTE |
-          HVP_MULTI_DIR | HVP_TENSOR))
+          HVP_MULTI_DIR | HVP_TENSOR | HVP_TRANSLATION))
         return fail(c, HVP_EINVAL, "unknown flag bits");
+    if ((cfg->flags & HVP_TRANSLATION) && (cfg->flags & HVP_MULTI_DIR))
+        return fail(c, HVP_EINVAL, "HVP_TRANSLATION cannot be combined with HVP_MULTI_DIR");
     if ((cfg->flags & HVP_TENSOR) &&
         (cfg->precision != HVP_C64 || (cfg->flags & (HVP_UNFUSED | HVP_MULTI_DIR | HVP_RECOMPUTE)) || n < 5))
         return fail(c, HVP_EINVAL, "HVP_TENSOR needs complex64, n >= 5 and none of HVP_UNFUSED, HVP_MULTI_DIR, "
@@ -731,7 +764,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         for (const auto& cand : cands) {
             const int wdw = cand[0], var = cand[2];
             hvp_config sc = *cfg;
-            sc.flags &= ~(HVP_AUTOTUNE | HVP_TENSOR);
+            sc.flags &= ~(HVP_AUTOTUNE | HVP_TENSOR | HVP_TRANSLATION);
             if (cand[3] == 1) sc.flags |= HVP_RECOMPUTE;
             if (cand[3] == 2) sc.flags |= HVP_TENSOR;
             sc.window = wdw >= n ? 0 : wdw;
@@ -802,7 +835,17 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     if ((rc = dalloc(c, &c->d_co, (multi ? 24 : state_elt(c)) * dim * ns))) return rc;
     if ((rc = dalloc(c, (void**)&c->d_partial, 64 * sizeof(double) * (size_t)c->K * ns * c->cx_count))) return rc;
     if ((rc = dalloc(c, (void**)&c->d_env, 64 * sizeof(double) * (size_t)c->K * ns))) return rc;
-    c->res_len = c->off_hr() + 32 * (size_t)c->K;
+    c->ti = (cfg->flags & HVP_TRANSLATION) != 0;
+    c->res_len = c->off_layer() + (c->ti ? 4 * 32 * (size_t)L : 0);
+    if (c->ti) {
+        std::vector<int> first(L + 1, 0);
+        for (int l = 0; l < L; ++l) first[l + 1] = first[l] + (n - l % 2) / 2;
+        if ((rc = dalloc(c, (void**)&c->d_GL, 16 * 16 * (size_t)L))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_VL, 16 * 16 * (size_t)L))) return rc;
+        if ((rc = dalloc(c, (void**)&c->d_layer_first, sizeof(int) * (L + 1)))) return rc;
+        CUDA_TRY(c, cudaMemcpy(c->d_layer_first, first.data(), sizeof(int) * (L + 1), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemset(c->d_VL, 0, 16 * 16 * (size_t)L));
+    }
     if ((rc = dalloc(c, (void**)&c->d_res, sizeof(double) * c->res_len))) return rc;
     if ((rc = dalloc(c, (void**)&c->d_status, sizeof(int)))) return rc;
     CUDA_TRY(c, cudaMemset(c->d_V, 0, 16 * 16 * (size_t)c->K));
@@ -960,13 +1003,14 @@ int call_impl(hvp_ctx* c, const double* G, const double* V, double* loss, double
         int rc = batch_call(c->batch, G, V, false, loss, grad, hvp_out, e);
         return rc ? fail(c, rc, e) : HVP_OK;
     }
-    const size_t n32 = 32 * (size_t)c->K;
+    const size_t n32 = 32 * c->n_user();
     const bool tan = V != nullptr;
     if (!all_finite(G, n32) || (tan && !all_finite(V, n32))) return fail(c, HVP_ENONFINITE, "G or V is not finite");
     std::memcpy(c->h_in, G, sizeof(double) * n32);
     if (tan) std::memcpy(c->h_in + n32, V, sizeof(double) * n32);
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, c->h_in, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
-    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->d_V, c->h_in + n32, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->in_G(), c->h_in, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
+    if (tan)
+        CUDA_TRY(c, cudaMemcpyAsync(c->in_V(), c->h_in + n32, sizeof(double) * n32, cudaMemcpyHostToDevice, c->stream));
     int rc = run(c, tan);
     if (rc) return rc;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_res, c->d_res, sizeof(double) * c->res_len, cudaMemcpyDeviceToHost, c->stream));
@@ -975,9 +1019,9 @@ int call_impl(hvp_ctx* c, const double* G, const double* V, double* loss, double
     if (*c->h_status & 2) return fail(c, HVP_ETIMEOUT, "a bounded wait for a forward-cache copy expired");
     if (*c->h_status) return fail(c, HVP_ENONFINITE, "a gate is singular or not finite");
     const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
-    const double* g = c->h_res + (riem ? c->off_gr() : c->off_ge());
-    const double* h = c->h_res + (riem ? c->off_hr() : c->off_he());
-    if (!all_finite(c->h_res, c->off_ge() + n32) || !all_finite(g, n32) || (tan && !all_finite(h, n32)))
+    const double* g = c->h_res + c->uoff(riem ? 2 : 0);
+    const double* h = c->h_res + c->uoff(riem ? 3 : 1);
+    if (!all_finite(c->h_res, c->off_ge()) || !all_finite(g, n32) || (tan && !all_finite(h, n32)))
         return fail(c, HVP_ENONFINITE, "non-finite result");
     if (loss) *loss = c->h_res[0];
     if (grad) std::memcpy(grad, g, sizeof(double) * n32);
@@ -1114,19 +1158,19 @@ int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* lo
         int rcb = batch_call(c->batch, G_dev, V_dev, true, loss_dev, grad_dev, hvp_dev, e);
         return rcb ? fail(c, rcb, e) : HVP_OK;
     }
-    const size_t n32 = 32 * (size_t)c->K;
+    const size_t n32 = 32 * c->n_user();
     const bool tan = V_dev != nullptr;
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
-    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->d_V, V_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->in_G(), G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->in_V(), V_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
     int rc = run(c, tan);
     if (rc) return rc;
     const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
     if (loss_dev) CUDA_TRY(c, cudaMemcpyAsync(loss_dev, c->d_res, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     if (grad_dev)
-        CUDA_TRY(c, cudaMemcpyAsync(grad_dev, c->d_res + (riem ? c->off_gr() : c->off_ge()), sizeof(double) * n32,
+        CUDA_TRY(c, cudaMemcpyAsync(grad_dev, c->d_res + c->uoff(riem ? 2 : 0), sizeof(double) * n32,
                                     cudaMemcpyDeviceToDevice, c->stream));
     if (hvp_dev && tan)
-        CUDA_TRY(c, cudaMemcpyAsync(hvp_dev, c->d_res + (riem ? c->off_hr() : c->off_he()), sizeof(double) * n32,
+        CUDA_TRY(c, cudaMemcpyAsync(hvp_dev, c->d_res + c->uoff(riem ? 3 : 1), sizeof(double) * n32,
                                     cudaMemcpyDeviceToDevice, c->stream));
     return HVP_OK;
 }
@@ -1164,9 +1208,10 @@ int hvp_hvp_multi_dev(hvp_ctx* c, const double* G_dev, int n_dir, const double* 
             }
         }
     }
+    const size_t nu32 = 32 * c->n_user();
     for (; d < n_dir; ++d) {   // one direction per sweep
-        int rc = hvp_hvp_dev(c, G_dev, V_dev + d * n32, d == 0 ? loss_dev : nullptr, d == 0 ? grad_dev : nullptr,
-                             hvp_dev ? hvp_dev + d * n32 : nullptr);
+        int rc = hvp_hvp_dev(c, G_dev, V_dev + d * nu32, d == 0 ? loss_dev : nullptr, d == 0 ? grad_dev : nullptr,
+                             hvp_dev ? hvp_dev + d * nu32 : nullptr);
         if (rc) return rc;
     }
     return HVP_OK;
@@ -1177,7 +1222,7 @@ int hvp_hvp_multi(hvp_ctx* c, const double* G, int n_dir, const double* V, doubl
     if (!c) return HVP_EINVAL;
     if (!G || !V || n_dir < 1) return fail(c, HVP_EINVAL, "hvp_hvp_multi: NULL input or n_dir < 1");
     if (c->batch) return fail(c, HVP_EINVAL, "hvp_hvp_multi: not available for a batch context");
-    const size_t n32 = 32 * (size_t)c->K;
+    const size_t n32 = 32 * c->n_user();
     if (!all_finite(G, n32) || !all_finite(V, n32 * n_dir)) return fail(c, HVP_ENONFINITE, "G or V is not finite");
     const bool riem = (c->cfg.flags & HVP_RIEMANNIAN) != 0;
     int d = 0;
@@ -1229,10 +1274,10 @@ int hvp_profile(hvp_ctx* c, const double* G_dev, const double* V_dev, int max_la
                 double* flops, double* bytes) {
     if (!c || !G_dev || max_launches < 0) return HVP_EINVAL;
     if (c->batch) return fail(c, HVP_EINVAL, "hvp_profile: not available for a batch context");
-    const size_t n32 = 32 * (size_t)c->K;
+    const size_t n32 = 32 * c->n_user();
     const bool tan = V_dev != nullptr;
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_G, G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
-    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->d_V, V_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->in_G(), G_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
+    if (tan) CUDA_TRY(c, cudaMemcpyAsync(c->in_V(), V_dev, sizeof(double) * n32, cudaMemcpyDeviceToDevice, c->stream));
     cudaEvent_t start;
     CUDA_TRY(c, cudaEventCreate(&start));
     CUDA_TRY(c, cudaEventRecord(start, c->stream));
@@ -1274,14 +1319,14 @@ int hvp_get(hvp_ctx* c, int what, double* out) {
         return rcb ? fail(c, rcb, e) : HVP_OK;
     }
     size_t off = 0, len = 0;
-    const size_t n32 = 32 * (size_t)c->K, ns = c->cfg.n_samples;
+    const size_t n32 = 32 * c->n_user(), ns = c->cfg.n_samples;
     switch (what) {
         case HVP_OUT_T: off = c->off_T(); len = 2 * ns; break;
         case HVP_OUT_OMEGA: off = c->off_Om(); len = 2 * ns; break;
-        case HVP_OUT_GRAD_E: off = c->off_ge(); len = n32; break;
-        case HVP_OUT_HVP_E: off = c->off_he(); len = n32; break;
-        case HVP_OUT_GRAD_R: off = c->off_gr(); len = n32; break;
-        case HVP_OUT_HVP_R: off = c->off_hr(); len = n32; break;
+        case HVP_OUT_GRAD_E: off = c->uoff(0); len = n32; break;
+        case HVP_OUT_HVP_E: off = c->uoff(1); len = n32; break;
+        case HVP_OUT_GRAD_R: off = c->uoff(2); len = n32; break;
+        case HVP_OUT_HVP_R: off = c->uoff(3); len = n32; break;
         case HVP_OUT_LOSS: off = 0; len = 1; break;
         case HVP_OUT_ENV:
             if (c->tensor)

@@ -474,7 +474,9 @@ struct BatchImpl {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int launches = 0;
 
-    size_t off_ge() const { return (size_t)nc; }
+    // the per-gate blocks are double2 arrays: start them on a 16-byte boundary
+    // after the nc losses (an odd nc would misalign them)
+    size_t off_ge() const { return ((size_t)nc + 1) & ~(size_t)1; }
     size_t off_he() const { return off_ge() + 32 * (size_t)sumK; }
     size_t off_gr() const { return off_he() + 32 * (size_t)sumK; }
     size_t off_hr() const { return off_gr() + 32 * (size_t)sumK; }

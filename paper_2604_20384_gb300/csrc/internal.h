@@ -251,6 +251,12 @@ struct PostArgs {
     int frobenius;          // 1: derivatives of C_F = 1 - mean Re T instead of C
 };
 cudaError_t launch_post(const PostArgs& p, cudaStream_t st);
+// App. E on the device: layer gates to every gate of the layer, and per-gate
+// derivative blocks (four K x 16 outputs, contiguous) to per-layer sums.
+cudaError_t launch_expand_layers(const double2* GL, const double2* VL, double2* G, double2* V, const int* first, int L,
+                                 cudaStream_t st);
+cudaError_t launch_contract_layers(const double2* per_gate, double2* per_layer, const int* first, int L, int K,
+                                   cudaStream_t st);
 // grad / HVP (Euclidean and App. F) and the loss from sample-summed weighted
 // environments (fused-block schedule).
 cudaError_t launch_post_weighted(const double2* Ew, const double2* DEw, const double2* G, const double2* V,

@@ -242,7 +242,49 @@ __global__ void phi_permute_kernel(const double2* __restrict__ in, void* out, in
     }
 }
 
+// Translation-invariant layers (App. E): every gate of layer l is the layer
+// gate G_l (and the direction V_l). One CTA of 16 threads per layer.
+__global__ void expand_layers_kernel(const double2* __restrict__ GL, const double2* __restrict__ VL,
+                                     double2* __restrict__ G, double2* __restrict__ V,
+                                     const int* __restrict__ first) {
+    const int l = blockIdx.x, e = threadIdx.x;
+    const double2 g = GL[l * 16 + e];
+    const double2 v = VL ? VL[l * 16 + e] : make_double2(0.0, 0.0);
+    for (int k = first[l]; k < first[l + 1]; ++k) {
+        G[k * 16 + e] = g;
+        if (VL) V[k * 16 + e] = v;
+    }
+}
+
+// The chain rule through the tying map of App. E: the derivative with respect
+// to a layer gate is the sum of the per-gate blocks of its layer (gradient
+// and HVP alike; the Riemannian forms are linear in those blocks at a fixed
+// layer gate, so they sum the same way). FP64, gates in circuit order. Grid
+// (layer, output): outputs 0..3 = Euclidean gradient, Euclidean HVP,
+// Riemannian gradient, Riemannian HVP, each K x 16 per gate in `in` and
+// n_layers x 16 per layer in `out`.
+__global__ void contract_layers_kernel(const double2* __restrict__ in, double2* __restrict__ out,
+                                       const int* __restrict__ first, int L, int K) {
+    const int l = blockIdx.x, which = blockIdx.y, e = threadIdx.x;
+    const double2* src = in + (size_t)which * K * 16;
+    double2 a = make_double2(0.0, 0.0);
+    for (int k = first[l]; k < first[l + 1]; ++k) a = dadd(a, src[k * 16 + e]);
+    out[((size_t)which * L + l) * 16 + e] = a;
+}
+
 }  // namespace
+
+cudaError_t launch_expand_layers(const double2* GL, const double2* VL, double2* G, double2* V, const int* first, int L,
+                                 cudaStream_t st) {
+    expand_layers_kernel<<<L, 16, 0, st>>>(GL, VL, G, V, first);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_layers(const double2* per_gate, double2* per_layer, const int* first, int L, int K,
+                                   cudaStream_t st) {
+    contract_layers_kernel<<<dim3(L, 4), 16, 0, st>>>(per_gate, per_layer, first, L, K);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_prep(const double2* G, const double2* V, void* mats, bool dbl, int K, int* status,
                         cudaStream_t st) {

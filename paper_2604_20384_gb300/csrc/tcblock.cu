@@ -43,8 +43,6 @@
 // mbarrier is bounded: a wait that gives up sets bit 2 of *status, the CTA
 // leaves its loop together, commits its MMAs in flight to a separate barrier
 // and waits (bounded) for it, then frees its TMEM.
-#include <mutex>
-
 #include "internal.h"
 
 namespace hvp {
@@ -61,14 +59,14 @@ constexpr int kFlushTiles = 16;              // FP32 tiles summed before an FP64
 constexpr unsigned kWaitLimit = 1u << 22;    // mbarrier polls before a wait gives up
 
 // Shared-memory regions (bytes): X slices (six per stage, K = 64 x 32
-// columns, bf16, strides up to LBO 192 / SBO 8 * 192 + 112) and, backward,
-// the forward-state tile (TF32 high and low, K = 32 columns x 128 rows).
-constexpr unsigned kXRegion = 6528;
-constexpr unsigned kERegion = 26240;
+// columns, bf16, with the strides below) and, backward, the forward-state
+// tile (TF32 high and low, K = 32 columns x 128 rows).
+constexpr unsigned kXRegion = 4608;
+constexpr unsigned kERegion = 16640;
 constexpr unsigned kStageFwd = 6 * kXRegion;
 constexpr unsigned kStageBwd = 6 * kXRegion + 2 * kERegion;
 constexpr unsigned kStagingBytes = TN * 32 * 16;
-constexpr unsigned kCtlBytes = 2 * 2 * 2 * 32 * 4 + 64;   // per stage: column maxima and scales; barriers
+constexpr unsigned kCtlBytes = 2 * 2 * 2 * 32 * 4 + 128;  // per stage: column maxima and scales; barriers
 constexpr unsigned smem_bytes(bool bwd) {
     return 2 * (bwd ? kStageBwd : kStageFwd) + kStagingBytes + kCtlBytes;
 }
@@ -76,11 +74,12 @@ constexpr unsigned smem_bytes(bool bwd) {
 // per SM (it holds all of the SM's TMEM).
 constexpr unsigned launch_smem(bool bwd) { return smem_bytes(bwd) > 116u * 1024u ? smem_bytes(bwd) : 116u * 1024u; }
 
-// Per-block strides of the staged operands (bytes), picked on the host (see
-// pick_strides) so that a warp's stores spread over the shared-memory banks.
-struct Strides {
-    unsigned lbo_x, sbo_x, lbo_e, sbo_e;
-};
+// Strides of the staged operands (bytes). X slices: K-cores (4 block indices
+// x re, im) 144 bytes apart, so that a warp's 4-byte stores of 32 block
+// indices of one column hit 32 banks; column cores 1152 apart. Psi tile:
+// K-cores (4 columns) 128 apart, row cores 1040 apart (65 16-byte units, so
+// that eight lanes' 16-byte stores land in eight bank groups).
+constexpr unsigned kLboX = 144, kSboX = 1152, kLboE = 128, kSboE = 1040;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -138,14 +137,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned par) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned par, unsigned limit) {
-    for (unsigned i = 0; i < limit; ++i)
-        if (mbar_try(bar, par)) return true;
-    return false;
-}
 
-// Bit-reversal of three bits: the staging-buffer swizzle.
-__device__ __forceinline__ unsigned rev3(unsigned q) { return ((q & 1u) << 2) | (q & 2u) | ((q >> 2) & 1u); }
 
 // Global amplitude index of block index b and column c: c = (sample, the
 // other n - 5 qubits in address order); the block's bits are [bl, bl + 5).
@@ -235,51 +227,71 @@ __device__ __forceinline__ void slice3(float y, uint32_t& b0, uint32_t& b1, uint
     b2 = __float_as_uint(s2) >> 16;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Barrier of the 256 worker threads (the MMA warp does not take part).
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Barriers in shared memory (mbarriers):
+enum : int {
+    B_FULL0 = 0,    // stage 0 staged (256 worker arrivals)
+    B_FULL1 = 1,    // stage 1 staged
+    B_DONE_U = 2,   // the tile's update MMAs complete (commit)
+    B_ACCFREE = 3,  // the workers have read the update accumulators (256 arrivals)
+    B_CREADY = 4,   // backward: the co-states are in TMEM as TF32 parts (256 arrivals)
+    B_DONE_E = 5,   // backward: the environment MMAs complete (commit)
+    B_DRAIN = 6,    // every MMA issued so far complete (commit, on the way out after a failed wait)
+    B_COUNT = 7
+};
+
+// Warp roles: warps 0-7 (256 threads) load, slice and stage the tiles, read
+// the accumulators and store results; warp 8 owns TMEM and its first lane
+// issues every MMA, so slicing the next tile overlaps this tile's MMAs.
 template <bool BWD>
-__global__ void __launch_bounds__(kT, 1) tcb_kernel(TcbArgs a, Strides st) {
+__global__ void __launch_bounds__(kT + 32, 1) tcb_kernel(TcbArgs a) {
     constexpr unsigned kStage = BWD ? kStageBwd : kStageFwd;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stagebuf = smem;                                   // [2][kStage]
     float* staging = reinterpret_cast<float*>(smem + 2 * kStage);     // epilogue output tile
-    unsigned* cmax = reinterpret_cast<unsigned*>(smem + 2 * kStage + kStagingBytes);   // [stage][group][32]
-    float* csc = reinterpret_cast<float*>(cmax + 2 * 2 * 32);                          // [stage][group][32]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(csc + 2 * 2 * 32);                    // [update, env, drain]
-    volatile unsigned* ctl = reinterpret_cast<volatile unsigned*>(bars + 3);          // [tmem base, stop]
+    float* csc = reinterpret_cast<float*>(smem + 2 * kStage + kStagingBytes);          // [stage][group][32]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(csc + 2 * 2 * 32);                    // [B_COUNT]
+    volatile unsigned* ctl = reinterpret_cast<volatile unsigned*>(bars + B_COUNT);    // [tmem base, stop]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == 8;
     const int n = a.n, bl = n - a.a - 5;
     const long long ncols = a.ncols;
     const long long ntiles = (ncols + TN - 1) / TN;
     const unsigned limit = a.wait_limit ? a.wait_limit : kWaitLimit;
     const bool tangent = !(a.mode & TCB_NO_TANGENT);
     const int nh = tangent ? 2 : 1;
-    const int qb = min(max(bl - 2, 0), 3);
     const int dir = BWD ? 1 : 0;
 
-    if (warp == 0) {
+    if (mma_warp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void*)ctl)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1u + a.barrier_extra));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1u + a.barrier_extra));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[2])));
+        const unsigned extra = a.barrier_extra;
+        const unsigned counts[B_COUNT] = {256u, 256u, 1u + extra, 256u, 256u, 1u + extra, 1u};
+        for (int i = 0; i < B_COUNT; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[i])), "r"(counts[i]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         ctl[1] = 0u;
     }
-    for (int i = tid; i < 2 * 2 * 32; i += kT) cmax[i] = 0u;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tb = ctl[0];
     const unsigned lane_base = (unsigned)((warp & 3) * 32) << 16;
-    const int row = (warp & 3) * 32 + lane;       // TMEM lane = output row 4 b' + p'
+    const int row = (warp & 3) * 32 + lane;       // TMEM lane = output row 4 b' + p' (worker warps)
 
     // Operator slices into TMEM: warps 0-3 the three slices of half 0, warps
     // 4-7 those of half 1; each thread its row (32 words = 64 bf16 per slice).
-    {
+    if (!mma_warp) {
         const int h = warp >> 2;
         for (int i = 0; i < 3; ++i) {
             const uint32_t* src = a.ops + ((dir * 2 + h) * 3 + i) * kOpSliceWords + row * 32;
@@ -290,236 +302,263 @@ __global__ void __launch_bounds__(kT, 1) tcb_kernel(TcbArgs a, Strides st) {
         }
         tmem_wait_st();
     }
-    const float* rsc = reinterpret_cast<const float*>(a.ops + kOpScaleOff) + dir * 256;
-    const float rs0 = __ldg(&rsc[row]), rs1 = __ldg(&rsc[128 + row]);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
-    // This thread's unit of a tile: block index b and column quad q (four
-    // columns 4q .. 4q + 3), in global address order.
-    const int qlo = tid & ((1 << qb) - 1);
-    const unsigned ub = (unsigned)((tid >> qb) & 31);
-    const int uq = qlo | ((tid >> (qb + 5)) << qb);
-    float4 xr[4], yr[BWD ? 4 : 1];
-    auto prefetch = [&](long long tile) {
-        const long long c0 = tile * TN;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const long long c = c0 + 4 * uq + i;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f), y = v;
-            if (c < ncols) {
-                const size_t g = amp_index(c, ub, n, bl);
-                if (!BWD) {
-                    if (a.mode & TCB_GEN) {
-                        const float2 p = product_amp(a.psi1q, g, n);
-                        v = make_float4(p.x, p.y, 0.f, 0.f);
-                    } else {
-                        v = __ldcs(&a.xin[g]);
-                    }
-                } else {
-                    if (a.mode & TCB_LOAD_PHI) {
-                        const float2 ph = __ldg(&a.phi[g]);
-                        const size_t s = g >> n;
-                        float2 w1 = make_float2(1.f, 0.f), w2 = make_float2(0.f, 0.f);
-                        if (a.w1) w1 = make_float2((float)a.w1[s].x, (float)a.w1[s].y);
-                        if (a.w2) w2 = make_float2((float)a.w2[s].x, (float)a.w2[s].y);
-                        v = make_float4(w1.x * ph.x - w1.y * ph.y, w1.x * ph.y + w1.y * ph.x,
-                                        w2.x * ph.x - w2.y * ph.y, w2.x * ph.y + w2.y * ph.x);
-                    } else {
-                        v = __ldcs(&a.xin[g]);
-                    }
-                    if (a.mode & TCB_GEN) {
-                        const float2 p = product_amp(a.psi1q, g, n);
-                        y = make_float4(p.x, p.y, 0.f, 0.f);
-                    } else {
-                        y = __ldcs(&a.psi[g]);
-                    }
+    // A wait that gives up raises the stop flag; every later wait sees it and
+    // returns at once, so all roles leave their loops.
+    auto wait = [&](int b, unsigned par) -> bool {
+        if (ctl[1]) return false;
+        for (unsigned i = 0; i < limit; ++i) {
+            if (mbar_try(&bars[b], par)) return true;
+            if ((i & 255u) == 255u && ctl[1]) return false;
+        }
+        ctl[1] = 1u;
+        atomicOr(a.status, 2);
+        return false;
+    };
+
+    if (mma_warp) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t id_u = idesc_bf16(TN), id_e = idesc_tf32(128);
+            const unsigned sbase = smem_u32(stagebuf);
+            const uint64_t kstep_x = (uint64_t)((2u * kLboX) >> 4);
+            const uint64_t kstep_e = (uint64_t)((2u * kLboE) >> 4);
+            bool issued = false;
+            long long i = 0;
+            for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+                const int sg = (int)(i & 1);
+                if (!wait(B_FULL0 + sg, (unsigned)((i >> 1) & 1))) break;
+                if (i > 0) {
+                    if (!wait(B_ACCFREE, (unsigned)((i - 1) & 1))) break;
+                    if (BWD && !wait(B_DONE_E, (unsigned)((i - 1) & 1))) break;
                 }
-                if (!tangent) { v.z = 0.f; v.w = 0.f; y.z = 0.f; y.w = 0.f; }
-            }
-            xr[i] = v;
-            if constexpr (BWD) yr[i] = y;
-        }
-    };
-    // Column maxima of the two component groups: warp-reduced over the lanes
-    // that hold the same column quad, then one shared-memory atomic per column.
-    auto colmax = [&](int sg) {
-        unsigned m[2][4];
+                tc_fence_after();
+                // D = A X: per half, levels 0..2 of slice products (i + j = level), 4 K-steps of 16.
+                const unsigned xs = sbase + sg * kStage;
+                for (int h = 0; h < nh; ++h)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            m[0][i] = __float_as_uint(fmaxf(fabsf(xr[i].x), fabsf(xr[i].y)));
-            m[1][i] = __float_as_uint(fmaxf(fabsf(xr[i].z), fabsf(xr[i].w)));
-        }
-        // lane bits [qb, min(qb + 5, 5)) are block-index bits: reduce over them
-        for (int j = qb; j < 5; ++j)
+                    for (int lev = 0; lev < 3; ++lev) {
+                        const unsigned d = tb + kAccCol + (h * 3 + lev) * 32;
 #pragma unroll
-            for (int g = 0; g < 2; ++g)
+                        for (int ii = 0; ii <= lev; ++ii) {
+                            const uint64_t bd = sdesc(xs + (h * 3 + lev - ii) * kXRegion, kLboX, kSboX);
+                            const unsigned ad = tb + kOpCol + (h * 3 + ii) * 32;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) m[g][i] = max(m[g][i], __shfl_xor_sync(0xffffffffu, m[g][i], 1 << j));
-        if ((lane >> qb) == 0)
-#pragma unroll
-            for (int g = 0; g < 2; ++g)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) atomicMax(&cmax[(sg * 2 + g) * 32 + 4 * uq + i], m[g][i]);
-    };
-    // Registers -> the slices of stage sg (column scales from cmax).
-    auto stage = [&](int sg) {
-        unsigned char* xb = stagebuf + sg * kStage;
-        unsigned char* eb = xb + 6 * kXRegion;
-        float up[2][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                const int e = col_exp(cmax[(sg * 2 + g) * 32 + 4 * uq + i]);
-                up[g][i] = pow2f(8 - e);
-            }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int col = 4 * uq + i;
-            const unsigned off = (unsigned)(col & 7) * 16u + (ub & 3u) * 4u + (ub >> 2) * st.lbo_x +
-                                 (unsigned)(col >> 3) * st.sbo_x;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h == 1 && !tangent) break;
-                const float re = (h ? xr[i].z : xr[i].x) * up[h][i], im = (h ? xr[i].w : xr[i].y) * up[h][i];
-                uint32_t r0, r1, r2, i0, i1, i2;
-                slice3(re, r0, r1, r2);
-                slice3(im, i0, i1, i2);
-                *reinterpret_cast<uint32_t*>(xb + (h * 3 + 0) * kXRegion + off) = r0 | (i0 << 16);
-                *reinterpret_cast<uint32_t*>(xb + (h * 3 + 1) * kXRegion + off) = r1 | (i1 << 16);
-                *reinterpret_cast<uint32_t*>(xb + (h * 3 + 2) * kXRegion + off) = r2 | (i2 << 16);
-            }
-        }
-        if constexpr (BWD) {
-            float4 hi[4], lo[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                hi[i] = make_float4(tf32_rna(yr[i].x), tf32_rna(yr[i].y), tf32_rna(yr[i].z), tf32_rna(yr[i].w));
-                lo[i] = make_float4(tf32_rna(yr[i].x - hi[i].x), tf32_rna(yr[i].y - hi[i].y),
-                                    tf32_rna(yr[i].z - hi[i].z), tf32_rna(yr[i].w - hi[i].w));
-            }
-            // Psi: rows 4 b + p, K = the tile's columns (4 per 16-byte row)
-            const unsigned base = (unsigned)uq * st.lbo_e + (ub >> 1) * st.sbo_e + (ub & 1u) * 64u;
-            unsigned char* eh = eb;
-            unsigned char* el = eb + kERegion;
-            *reinterpret_cast<float4*>(eh + base + 0) = make_float4(hi[0].x, hi[1].x, hi[2].x, hi[3].x);
-            *reinterpret_cast<float4*>(eh + base + 16) = make_float4(hi[0].y, hi[1].y, hi[2].y, hi[3].y);
-            *reinterpret_cast<float4*>(eh + base + 32) = make_float4(hi[0].z, hi[1].z, hi[2].z, hi[3].z);
-            *reinterpret_cast<float4*>(eh + base + 48) = make_float4(hi[0].w, hi[1].w, hi[2].w, hi[3].w);
-            *reinterpret_cast<float4*>(el + base + 0) = make_float4(lo[0].x, lo[1].x, lo[2].x, lo[3].x);
-            *reinterpret_cast<float4*>(el + base + 16) = make_float4(lo[0].y, lo[1].y, lo[2].y, lo[3].y);
-            *reinterpret_cast<float4*>(el + base + 32) = make_float4(lo[0].z, lo[1].z, lo[2].z, lo[3].z);
-            *reinterpret_cast<float4*>(el + base + 48) = make_float4(lo[0].w, lo[1].w, lo[2].w, lo[3].w);
-        }
-        // column scales of the stage for the epilogue
-        if (tid < 64) csc[sg * 64 + tid] = pow2f(col_exp(cmax[sg * 64 + tid]) - 8);
-        fence_async_smem();
-    };
-
-    float acc[BWD ? 64 : 1];
-#pragma unroll
-    for (int i = 0; i < (BWD ? 64 : 1); ++i) acc[i] = 0.f;
-    int since_flush = 0;
-    bool flushed = false;
-    auto flush = [&]() {
-        if constexpr (BWD) {
-            double* dst = a.rec + (size_t)blockIdx.x * 16384 + (size_t)row * 128 + 64 * (warp >> 2);
-#pragma unroll
-            for (int i = 0; i < 64; i += 2) {
-                double2 o = make_double2(0.0, 0.0);
-                if (flushed) o = *reinterpret_cast<double2*>(dst + i);
-                o.x += (double)acc[i];
-                o.y += (double)acc[i + 1];
-                *reinterpret_cast<double2*>(dst + i) = o;
-                acc[i] = 0.f;
-                acc[i + 1] = 0.f;
-            }
-            flushed = true;
-            since_flush = 0;
-        }
-    };
-
-    const uint32_t id_u = idesc_bf16(TN), id_e = idesc_tf32(128);
-    const unsigned sbase = smem_u32(stagebuf);
-    unsigned parity = 0, pend = 0;   // pend (thread 0): commits whose completion it has not seen
-    bool stop = false;
-    long long tile = blockIdx.x;
-    int sg = 0;
-    if (tile < ntiles) {
-        prefetch(tile);
-        colmax(0);
-        __syncthreads();
-        stage(0);
-    }
-    for (; tile < ntiles; tile += gridDim.x) {
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            // D = A X: per half, levels 0..2 of slice products (i + j = level), 4 K-steps of 16.
-            const unsigned xs = sbase + sg * kStage;
-            const uint64_t kstep = (uint64_t)((2u * st.lbo_x) >> 4);
-            for (int h = 0; h < nh; ++h)
-#pragma unroll
-                for (int lev = 0; lev < 3; ++lev) {
-                    int first = 1;
-#pragma unroll
-                    for (int i = 0; i <= lev; ++i) {
-                        const int j = lev - i;
-                        const uint64_t bd = sdesc(xs + (h * 3 + j) * kXRegion, st.lbo_x, st.sbo_x);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            mma_ts_f16(tb + kAccCol + (h * 3 + lev) * 32, tb + kOpCol + (h * 3 + i) * 32 + 8 * k,
-                                       bd + k * kstep, id_u, first ? 0 : 1);
-                            first = 0;
+                            for (int k = 0; k < 4; ++k)
+                                mma_ts_f16(d, ad + 8 * k, bd + k * kstep_x, id_u, (ii | k) != 0);
                         }
                     }
-                }
-            mma_commit(&bars[0]);
-            pend |= 1u;
-        }
-        // the next tile: loads, column maxima and slices into the other stage
-        const long long next = tile + gridDim.x;
-        if (next < ntiles) {
-            prefetch(next);
-            colmax(sg ^ 1);
-            __syncthreads();
-            stage(sg ^ 1);
-        }
-        if (!mbar_wait(&bars[0], parity, limit)) {
-            ctl[1] = 1u;
-            atomicOr(a.status, 2);
-        } else {
-            pend &= ~1u;
-        }
-        tc_fence_after();
-        __syncthreads();
-        if (ctl[1]) { stop = true; break; }
-
-        // Epilogue: combine the levels; D -> staging (and, backward, TMEM as TF32 high / low parts).
-        const long long c0 = tile * TN;
-        {
-            const int cc = (warp >> 2) * 16;   // this thread's 16 columns
-            float l[2][3][16];
+                mma_commit(&bars[B_DONE_U]);
+                issued = true;
+                if constexpr (BWD) {
+                    if (!wait(B_CREADY, (unsigned)(i & 1))) break;
+                    tc_fence_after();
+                    // P = D Psi^T: K = the tile's 32 columns, 4 K-steps; A = D (high, low) from TMEM.
+                    const unsigned eb = sbase + sg * kStage + 6 * kXRegion;
+                    const uint64_t ph = sdesc(eb, kLboE, kSboE), pl = sdesc(eb + kERegion, kLboE, kSboE);
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int lev = 0; lev < 3; ++lev) {
-                    if (h == 1 && !tangent) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) l[h][lev][j] = 0.f;
-                    } else {
-                        tmem_ld16(tb + lane_base + kAccCol + (h * 3 + lev) * 32 + cc, l[h][lev]);
+                    for (int k = 0; k < TN / 8; ++k) {
+                        mma_ts(tb + kEnvCol, tb + kAccCol + 8 * k, ph + k * kstep_e, id_e, k > 0);
+                        mma_ts(tb + kEnvCol, tb + kAccCol + 8 * k, pl + k * kstep_e, id_e, 1);
+                        mma_ts(tb + kEnvCol, tb + kAccCol + 32 + 8 * k, ph + k * kstep_e, id_e, 1);
                     }
+                    mma_commit(&bars[B_DONE_E]);
                 }
+            }
+            if (ctl[1] && issued) {   // let every MMA issued so far finish (bounded) before TMEM is freed
+                mma_commit(&bars[B_DRAIN]);
+                for (unsigned k = 0; k < kWaitLimit; ++k)
+                    if (mbar_try(&bars[B_DRAIN], 0u)) break;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ workers
+        // Warp w owns the tile's column quad w (columns 4w .. 4w + 3), lane l
+        // the block index b = l: a lane loads four columns of one block
+        // amplitude (full 32-byte sectors at every block position), and the
+        // column maxima are warp reductions.
+        const unsigned ub = (unsigned)lane;
+        const int uq = warp;
+        float4 xr[4], yr[BWD ? 4 : 1];
+        float up[2][4];   // per column and component group: 2^(8 - e), e the column's scale exponent
+        auto prefetch = [&](long long tile) {
+            const long long c0 = tile * TN;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const long long c = c0 + 4 * uq + i;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f), y = v;
+                if (c < ncols) {
+                    const size_t g = amp_index(c, ub, n, bl);
+                    if (!BWD) {
+                        if (a.mode & TCB_GEN) {
+                            const float2 p = product_amp(a.psi1q, g, n);
+                            v = make_float4(p.x, p.y, 0.f, 0.f);
+                        } else {
+                            v = __ldcs(&a.xin[g]);
+                        }
+                    } else {
+                        if (a.mode & TCB_LOAD_PHI) {
+                            const float2 ph = __ldg(&a.phi[g]);
+                            const size_t s = g >> n;
+                            float2 w1 = make_float2(1.f, 0.f), w2 = make_float2(0.f, 0.f);
+                            if (a.w1) w1 = make_float2((float)a.w1[s].x, (float)a.w1[s].y);
+                            if (a.w2) w2 = make_float2((float)a.w2[s].x, (float)a.w2[s].y);
+                            v = make_float4(w1.x * ph.x - w1.y * ph.y, w1.x * ph.y + w1.y * ph.x,
+                                            w2.x * ph.x - w2.y * ph.y, w2.x * ph.y + w2.y * ph.x);
+                        } else {
+                            v = __ldcs(&a.xin[g]);
+                        }
+                        if (a.mode & TCB_GEN) {
+                            const float2 p = product_amp(a.psi1q, g, n);
+                            y = make_float4(p.x, p.y, 0.f, 0.f);
+                        } else {
+                            y = __ldcs(&a.psi[g]);
+                        }
+                    }
+                    if (!tangent) { v.z = 0.f; v.w = 0.f; y.z = 0.f; y.w = 0.f; }
+                }
+                xr[i] = v;
+                if constexpr (BWD) yr[i] = y;
+            }
+        };
+        // Scale exponents of this warp's four columns (two component groups
+        // each): warp-wide maxima; lane 0 publishes the epilogue's scales.
+        auto colscale = [&](int sg) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const unsigned m0 = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(xr[i].x), fabsf(xr[i].y))));
+                const unsigned m1 = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(xr[i].z), fabsf(xr[i].w))));
+                const int e0 = col_exp(m0), e1 = col_exp(m1);
+                up[0][i] = pow2f(8 - e0);
+                up[1][i] = pow2f(8 - e1);
+                if (lane == 0) {
+                    csc[sg * 64 + 4 * uq + i] = pow2f(e0 - 8);
+                    csc[sg * 64 + 32 + 4 * uq + i] = pow2f(e1 - 8);
+                }
+            }
+        };
+        // Registers -> the slices of stage sg.
+        auto stage = [&](int sg) {
+            unsigned char* xb = stagebuf + sg * kStage;
+            unsigned char* eb = xb + 6 * kXRegion;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int col = 4 * uq + i;
+                const unsigned off = (unsigned)(col & 7) * 16u + (ub & 3u) * 4u + (ub >> 2) * kLboX +
+                                     (unsigned)(col >> 3) * kSboX;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !tangent) break;
+                    const float re = (h ? xr[i].z : xr[i].x) * up[h][i], im = (h ? xr[i].w : xr[i].y) * up[h][i];
+                    uint32_t r0, r1, r2, i0, i1, i2;
+                    slice3(re, r0, r1, r2);
+                    slice3(im, i0, i1, i2);
+                    *reinterpret_cast<uint32_t*>(xb + (h * 3 + 0) * kXRegion + off) = r0 | (i0 << 16);
+                    *reinterpret_cast<uint32_t*>(xb + (h * 3 + 1) * kXRegion + off) = r1 | (i1 << 16);
+                    *reinterpret_cast<uint32_t*>(xb + (h * 3 + 2) * kXRegion + off) = r2 | (i2 << 16);
+                }
+            }
+            if constexpr (BWD) {
+                float4 hi[4], lo[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    hi[i] = make_float4(tf32_rna(yr[i].x), tf32_rna(yr[i].y), tf32_rna(yr[i].z), tf32_rna(yr[i].w));
+                    lo[i] = make_float4(tf32_rna(yr[i].x - hi[i].x), tf32_rna(yr[i].y - hi[i].y),
+                                        tf32_rna(yr[i].z - hi[i].z), tf32_rna(yr[i].w - hi[i].w));
+                }
+                // Psi: rows 4 b + p, K = the tile's columns (4 per 16-byte row)
+                const unsigned base = (unsigned)uq * kLboE + (ub >> 1) * kSboE + (ub & 1u) * 64u;
+                unsigned char* eh = eb;
+                unsigned char* el = eb + kERegion;
+                *reinterpret_cast<float4*>(eh + base + 0) = make_float4(hi[0].x, hi[1].x, hi[2].x, hi[3].x);
+                *reinterpret_cast<float4*>(eh + base + 16) = make_float4(hi[0].y, hi[1].y, hi[2].y, hi[3].y);
+                *reinterpret_cast<float4*>(eh + base + 32) = make_float4(hi[0].z, hi[1].z, hi[2].z, hi[3].z);
+                *reinterpret_cast<float4*>(eh + base + 48) = make_float4(hi[0].w, hi[1].w, hi[2].w, hi[3].w);
+                *reinterpret_cast<float4*>(el + base + 0) = make_float4(lo[0].x, lo[1].x, lo[2].x, lo[3].x);
+                *reinterpret_cast<float4*>(el + base + 16) = make_float4(lo[0].y, lo[1].y, lo[2].y, lo[3].y);
+                *reinterpret_cast<float4*>(el + base + 32) = make_float4(lo[0].z, lo[1].z, lo[2].z, lo[3].z);
+                *reinterpret_cast<float4*>(el + base + 48) = make_float4(lo[0].w, lo[1].w, lo[2].w, lo[3].w);
+            }
+            fence_async_smem();
+        };
+        // one tile into stage sg: loads, column scales, slices; then the stage is announced
+        auto produce = [&](long long tile, int sg) {
+            prefetch(tile);
+            colscale(sg);
+            stage(sg);
+            mbar_arrive(&bars[B_FULL0 + sg]);
+        };
+
+        const float* rsc = reinterpret_cast<const float*>(a.ops + kOpScaleOff) + dir * 256;
+        const float rs0 = __ldg(&rsc[row]), rs1 = __ldg(&rsc[128 + row]);
+        float acc[BWD ? 64 : 1];
+#pragma unroll
+        for (int i = 0; i < (BWD ? 64 : 1); ++i) acc[i] = 0.f;
+        int since_flush = 0;
+        bool flushed = false;
+        auto flush = [&]() {
+            if constexpr (BWD) {
+                double* dst = a.rec + (size_t)blockIdx.x * 16384 + (size_t)row * 128 + 64 * (warp >> 2);
+#pragma unroll
+                for (int i = 0; i < 64; i += 2) {
+                    double2 o = make_double2(0.0, 0.0);
+                    if (flushed) o = *reinterpret_cast<double2*>(dst + i);
+                    o.x += (double)acc[i];
+                    o.y += (double)acc[i + 1];
+                    *reinterpret_cast<double2*>(dst + i) = o;
+                    acc[i] = 0.f;
+                    acc[i + 1] = 0.f;
+                }
+                flushed = true;
+                since_flush = 0;
+            }
+        };
+
+        long long i = 0;
+        bool ok = true;
+        if ((long long)blockIdx.x < ntiles) produce(blockIdx.x, 0);
+        for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+            const int sg = (int)(i & 1);
+            const long long next = tile + gridDim.x;
+            // the next tile into the other stage, while the MMAs of this one run
+            if (next < ntiles) produce(next, sg ^ 1);
+            // every worker waits; then all leave together if any wait gave up
+            wait(B_DONE_U, (unsigned)(i & 1));
+            workers_sync();
+            if (ctl[1]) { ok = false; break; }
+            tc_fence_after();
+
+            // Epilogue: combine the levels; D -> staging (and, backward, TMEM as TF32 high / low parts).
+            const int cc = (warp >> 2) * 16;   // this thread's 16 columns
             const unsigned bb = (unsigned)row >> 2, p = (unsigned)row & 3u;
             float v[16];
+            {
+                float l0[16], l1[16], l2[16];
+                tmem_ld16(tb + lane_base + kAccCol + 0 * 32 + cc, l0);
+                tmem_ld16(tb + lane_base + kAccCol + 1 * 32 + cc, l1);
+                tmem_ld16(tb + lane_base + kAccCol + 2 * 32 + cc, l2);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = rs0 * csc[sg * 64 + cc + j] *
+                           ((l0[j] + l1[j] * (1.f / 256.f)) + l2[j] * (1.f / 65536.f));
+                if (tangent) {
+                    tmem_ld16(tb + lane_base + kAccCol + 3 * 32 + cc, l0);
+                    tmem_ld16(tb + lane_base + kAccCol + 4 * 32 + cc, l1);
+                    tmem_ld16(tb + lane_base + kAccCol + 5 * 32 + cc, l2);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        v[j] += rs1 * csc[sg * 64 + 32 + cc + j] *
+                                ((l0[j] + l1[j] * (1.f / 256.f)) + l2[j] * (1.f / 65536.f));
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int col = cc + j;
-                const float d0 = (l[0][0][j] + l[0][1][j] * (1.f / 256.f)) + l[0][2][j] * (1.f / 65536.f);
-                const float d1 = (l[1][0][j] + l[1][1][j] * (1.f / 256.f)) + l[1][2][j] * (1.f / 65536.f);
-                v[j] = rs0 * csc[sg * 64 + col] * d0 + rs1 * csc[sg * 64 + 32 + col] * d1;
-                staging[(((unsigned)col * 32u + (bb ^ rev3(((unsigned)col >> 2) & 7u))) << 2) + p] = v[j];
+                const unsigned col = (unsigned)(cc + j);
+                staging[((col * 32u + bb) << 2) + p] = v[j];
             }
             if constexpr (BWD) {
                 float lo[16];
@@ -532,142 +571,50 @@ __global__ void __launch_bounds__(kT, 1) tcb_kernel(TcbArgs a, Strides st) {
                 tmem_st16(tb + lane_base + kAccCol + 0 * 32 + cc, v);
                 tmem_st16(tb + lane_base + kAccCol + 1 * 32 + cc, lo);
                 tmem_wait_st();
+                tc_fence_before();
+                mbar_arrive(&bars[B_CREADY]);
             }
-        }
-        tc_fence_before();
-        __syncthreads();
-        if constexpr (BWD) {
-            if (tid == 0) {
+            tc_fence_before();
+            mbar_arrive(&bars[B_ACCFREE]);
+            workers_sync();   // the staging tile is complete
+
+            // Staging -> global (overlaps the environment GEMM and the next tile's MMAs).
+            if (!(BWD && (a.mode & TCB_NO_STORE))) {
+                const unsigned sw = ub;
+                const long long c0 = tile * TN;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long c = c0 + 4 * uq + k;
+                    if (c < ncols) {
+                        const unsigned col = (unsigned)(4 * uq + k);
+                        const float4 o = *reinterpret_cast<const float4*>(staging + ((col * 32u + sw) << 2));
+                        __stcs(&a.xout[amp_index(c, ub, n, bl)], o);
+                    }
+                }
+            }
+            if constexpr (BWD) {
+                wait(B_DONE_E, (unsigned)(i & 1));
+                workers_sync();
+                if (ctl[1]) { ok = false; break; }
                 tc_fence_after();
-                // P = D Psi^T: K = the tile's 32 columns, 4 K-steps; A = D (high, low) from TMEM.
-                const unsigned eb = sbase + sg * kStage + 6 * kXRegion;
-                const uint64_t ph = sdesc(eb, st.lbo_e, st.sbo_e), pl = sdesc(eb + kERegion, st.lbo_e, st.sbo_e);
-                const uint64_t kstep = (uint64_t)((2u * st.lbo_e) >> 4);
+                float e[32];
+                tmem_ld32(tb + lane_base + kEnvCol + 64 * (warp >> 2), e);
 #pragma unroll
-                for (int k = 0; k < TN / 8; ++k) {
-                    mma_ts(tb + kEnvCol, tb + kAccCol + 8 * k, ph + k * kstep, id_e, k > 0);
-                    mma_ts(tb + kEnvCol, tb + kAccCol + 8 * k, pl + k * kstep, id_e, 1);
-                    mma_ts(tb + kEnvCol, tb + kAccCol + 32 + 8 * k, ph + k * kstep, id_e, 1);
-                }
-                mma_commit(&bars[1]);
-                pend |= 2u;
+                for (int j = 0; j < 32; ++j) acc[j] += e[j];
+                tmem_ld32(tb + lane_base + kEnvCol + 64 * (warp >> 2) + 32, e);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[32 + j] += e[j];
+                tc_fence_before();
+                if (++since_flush == kFlushTiles) flush();
             }
+            workers_sync();   // the staging tile is reused by the next iteration
         }
-        // Staging -> global (overlaps the environment GEMM).
-        if (!(BWD && (a.mode & TCB_NO_STORE))) {
-            const unsigned sw = ub ^ rev3((unsigned)uq & 7u);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const long long c = c0 + 4 * uq + i;
-                if (c < ncols) {
-                    const unsigned col = (unsigned)(4 * uq + i);
-                    const float4 v = *reinterpret_cast<const float4*>(staging + ((col * 32u + sw) << 2));
-                    __stcs(&a.xout[amp_index(c, ub, n, bl)], v);
-                }
-            }
-        }
-        if constexpr (BWD) {
-            if (!mbar_wait(&bars[1], parity, limit)) {
-                ctl[1] = 1u;
-                atomicOr(a.status, 2);
-            } else {
-                pend &= ~2u;
-            }
-            tc_fence_after();
-            float v[32];
-            tmem_ld32(tb + lane_base + kEnvCol + 64 * (warp >> 2), v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] += v[j];
-            tmem_ld32(tb + lane_base + kEnvCol + 64 * (warp >> 2) + 32, v);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[32 + j] += v[j];
-            if (++since_flush == kFlushTiles) flush();
-        }
-        // this stage's column maxima are consumed: clear them for its next tile
-        if (tid < 64) cmax[sg * 64 + tid] = 0u;
-        tc_fence_before();
-        __syncthreads();
-        if (ctl[1]) { stop = true; break; }
-        parity ^= 1u;
-        sg ^= 1;
-    }
-    if (stop) {   // a wait gave up: let every MMA issued so far finish (bounded) before freeing TMEM
-        if (tid == 0 && pend) {
-            mma_commit(&bars[2]);
-            mbar_wait(&bars[2], 0u, kWaitLimit);
-        }
-    } else if (BWD && (since_flush > 0 || !flushed)) {
-        flush();
+        if (ok && BWD && (since_flush > 0 || !flushed)) flush();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(kTmemCols));
-}
-
-// ------------------------------------------------------------ host: strides
-
-// Bank conflicts of one warp's stores for the strides s, for block-position
-// parameter qb (quad bits below the block): the X slices are written with
-// 4-byte stores at (col % 8) 16 + (b % 4) 4 + (b / 4) LBO + (col / 8) SBO, the
-// forward-state tile with 16-byte stores at q LBO_e + (b / 2) SBO_e + (b % 2)
-// 64 + p 16. Returns the summed wavefronts beyond the minimum.
-long conflicts(const Strides& s, int qb, bool bwd) {
-    long extra = 0;
-    for (int w = 0; w < 8; ++w) {
-        unsigned bs[32], qs[32];
-        for (int l = 0; l < 32; ++l) {
-            const int t = 32 * w + l;
-            bs[l] = (unsigned)((t >> qb) & 31);
-            qs[l] = (unsigned)((t & ((1 << qb) - 1)) | ((t >> (qb + 5)) << qb));
-        }
-        for (int i = 0; i < 4; ++i) {
-            int cnt[32] = {0};
-            for (int l = 0; l < 32; ++l) {
-                const unsigned col = 4 * qs[l] + i;
-                const unsigned addr = (col & 7) * 16 + (bs[l] & 3) * 4 + (bs[l] >> 2) * s.lbo_x + (col >> 3) * s.sbo_x;
-                ++cnt[(addr / 4) % 32];
-            }
-            int mx = 0;
-            for (int k = 0; k < 32; ++k) mx = std::max(mx, cnt[k]);
-            extra += mx - 1;
-        }
-        if (!bwd) continue;
-        for (int ph = 0; ph < 4; ++ph) {
-            int cnt[8] = {0};
-            for (int l = 8 * ph; l < 8 * ph + 8; ++l) {
-                const unsigned addr = qs[l] * s.lbo_e + (bs[l] >> 1) * s.sbo_e + (bs[l] & 1) * 64;
-                ++cnt[(addr / 16) % 8];
-            }
-            int mx = 0;
-            for (int k = 0; k < 8; ++k) mx = std::max(mx, cnt[k]);
-            extra += 4 * (mx - 1);   // four stores (components) per lane
-        }
-    }
-    return extra;
-}
-
-Strides pick_strides(int qb, bool bwd) {
-    static std::mutex mu;
-    static bool done[2][4] = {};
-    static Strides cache[2][4];
-    std::lock_guard<std::mutex> lock(mu);
-    if (done[bwd][qb]) return cache[bwd][qb];
-    Strides best{128, 1024, 128, 1024};
-    long best_c = -1;
-    // K-direction core strides of 128 .. 192 bytes, M/N-direction strides of
-    // 8 K-cores plus 0 .. 112 bytes (the regions' sizes assume these bounds).
-    for (unsigned lx = 128; lx <= 192; lx += 16)
-        for (unsigned jx = 0; jx <= 112; jx += 16)
-            for (unsigned le = 128; le <= (bwd ? 192u : 128u); le += 16)
-                for (unsigned je = 0; je <= (bwd ? 112u : 0u); je += 16) {
-                    Strides s{lx, 8 * lx + jx, le, 8 * le + je};
-                    const long c = conflicts(s, qb, bwd);
-                    if (best_c < 0 || c < best_c) { best_c = c; best = s; }
-                }
-    cache[bwd][qb] = best;
-    done[bwd][qb] = true;
-    return best;
+    if (mma_warp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(kTmemCols));
 }
 
 }  // namespace
@@ -683,11 +630,9 @@ cudaError_t tcb_set_smem_limits() {
 
 cudaError_t launch_tcb(const TcbArgs& a, bool bwd, int ctas, cudaStream_t st) {
     if (a.n < 5 || a.a < 0 || a.a + 5 > a.n || ctas < 1) return cudaErrorInvalidValue;
-    const int qb = std::min(std::max(a.n - a.a - 5 - 2, 0), 3);
-    const Strides s = pick_strides(qb, bwd);
     const unsigned smem = launch_smem(bwd);
-    if (bwd) tcb_kernel<true><<<ctas, kT, smem, st>>>(a, s);
-    else tcb_kernel<false><<<ctas, kT, smem, st>>>(a, s);
+    if (bwd) tcb_kernel<true><<<ctas, kT + 32, smem, st>>>(a);
+    else tcb_kernel<false><<<ctas, kT + 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

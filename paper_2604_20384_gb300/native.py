@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hvp.h")
 HVP_OK, HVP_EINVAL, HVP_ENOMEM, HVP_ECUDA, HVP_ETIMEOUT, HVP_ENONFINITE = 0, -1, -2, -3, -4, -5
 HVP_C64, HVP_C128 = 0, 1
 HVP_RIEMANNIAN, HVP_PHI_GIVEN, HVP_UNFUSED, HVP_NO_GRAPH, HVP_AUTOTUNE, HVP_FROBENIUS = 1, 2, 4, 8, 16, 32
-HVP_RECOMPUTE, HVP_MULTI_DIR, HVP_TENSOR = 64, 128, 256
+HVP_RECOMPUTE, HVP_MULTI_DIR, HVP_TENSOR, HVP_TRANSLATION = 64, 128, 256, 512
 KINDS = {0: "prep", 1: "pass_fwd", 2: "pass_turnaround", 3: "pass_bwd", 4: "gate_init", 5: "gate_fwd",
          6: "gate_load_phi", 7: "gate_bwd", 8: "post", 9: "block_fwd", 10: "block_bwd"}
 OUT = dict(T=1, Omega=2, grad_e=3, hvp_e=4, grad_r=5, hvp_r=6, loss=7, env=8)
@@ -170,16 +170,19 @@ class Context:
                  riemannian: bool = False, phi_given: bool = False, unfused: bool = False,
                  graphs: bool = True, checkpoint_stride: int = 0, window: int = 0, threads: int = 0,
                  variant: int = 0, autotune: bool = False, frobenius: bool = False, recompute: bool = False,
-                 multi_dir: bool = False, tensor: bool = False, device: int = 0, stream: int | None = None):
+                 multi_dir: bool = False, tensor: bool = False, translation: bool = False, device: int = 0,
+                 stream: int | None = None):
         self._lib = load()
         psi1q = np.asarray(psi1q)
         self.n, self.n_layers, self.n_samples = n, n_layers, int(psi1q.shape[0])
         self.K = self._lib.hvp_num_gates(n, n_layers)
+        # blocks per call the caller passes and receives: layers (HVP_TRANSLATION) or gates
+        self.blocks = n_layers if translation else self.K
         flags = ((HVP_RIEMANNIAN if riemannian else 0) | (HVP_PHI_GIVEN if phi_given else 0)
                  | (HVP_UNFUSED if unfused else 0) | (0 if graphs else HVP_NO_GRAPH)
                  | (HVP_AUTOTUNE if autotune else 0) | (HVP_FROBENIUS if frobenius else 0)
                  | (HVP_RECOMPUTE if recompute else 0) | (HVP_MULTI_DIR if multi_dir else 0)
-                 | (HVP_TENSOR if tensor else 0))
+                 | (HVP_TENSOR if tensor else 0) | (HVP_TRANSLATION if translation else 0))
         cfg = HVPConfig(n, n_layers, self.n_samples, HVP_C128 if precision == "c128" else HVP_C64, flags,
                         checkpoint_stride, window, threads, variant, device, stream)
         self._psi = _f64(psi1q)
@@ -199,18 +202,18 @@ class Context:
     def loss_grad(self, G):
         G = _f64(G)
         loss = np.zeros(1)
-        grad = np.zeros(32 * self.K)
+        grad = np.zeros(32 * self.blocks)
         self._check(self._lib.hvp_loss_grad(self._h, _ptr(G), _ptr(loss), _ptr(grad)))
-        return float(loss[0]), grad.view(np.complex128).reshape(self.K, 4, 4)
+        return float(loss[0]), grad.view(np.complex128).reshape(self.blocks, 4, 4)
 
     def hvp(self, G, V):
         G, V = _f64(G), _f64(V)
         loss = np.zeros(1)
-        grad = np.zeros(32 * self.K)
-        hv = np.zeros(32 * self.K)
+        grad = np.zeros(32 * self.blocks)
+        hv = np.zeros(32 * self.blocks)
         self._check(self._lib.hvp_hvp(self._h, _ptr(G), _ptr(V), _ptr(loss), _ptr(grad), _ptr(hv)))
-        return (float(loss[0]), grad.view(np.complex128).reshape(self.K, 4, 4),
-                hv.view(np.complex128).reshape(self.K, 4, 4))
+        return (float(loss[0]), grad.view(np.complex128).reshape(self.blocks, 4, 4),
+                hv.view(np.complex128).reshape(self.blocks, 4, 4))
 
     def hvp_multi(self, G, Vs):
         """(loss, grad, [HVP along each direction]) at the same gates
@@ -220,11 +223,11 @@ class Context:
         nd = int(Vs.shape[0])
         V = _f64(Vs)
         loss = np.zeros(1)
-        grad = np.zeros(32 * self.K)
-        hv = np.zeros(32 * self.K * nd)
+        grad = np.zeros(32 * self.blocks)
+        hv = np.zeros(32 * self.blocks * nd)
         self._check(self._lib.hvp_hvp_multi(self._h, _ptr(G), nd, _ptr(V), _ptr(loss), _ptr(grad), _ptr(hv)))
-        return (float(loss[0]), grad.view(np.complex128).reshape(self.K, 4, 4),
-                hv.view(np.complex128).reshape(nd, self.K, 4, 4))
+        return (float(loss[0]), grad.view(np.complex128).reshape(self.blocks, 4, 4),
+                hv.view(np.complex128).reshape(nd, self.blocks, 4, 4))
 
     def hvp_multi_dev(self, G_ptr: int, n_dir: int, V_ptr: int, loss_ptr: int | None, grad_ptr: int | None,
                       hvp_ptr: int | None):
@@ -252,7 +255,7 @@ class Context:
     def get(self, what: str):
         sizes = dict(T=2 * self.n_samples, Omega=2 * self.n_samples, loss=1,
                      env=64 * self.K * self.n_samples)
-        m = sizes.get(what, 32 * self.K)
+        m = sizes.get(what, 32 * self.blocks)
         out = np.zeros(m)
         self._check(self._lib.hvp_get(self._h, OUT[what], _ptr(out)))
         if what == "loss":
@@ -263,7 +266,7 @@ class Context:
         if what == "env":
             e = c.reshape(self.n_samples, self.K, 2, 4, 4)
             return e[:, :, 0], e[:, :, 1]
-        return c.reshape(self.K, 4, 4)
+        return c.reshape(self.blocks, 4, 4)
 
     def plan_info(self) -> dict:
         info = (ctypes.c_longlong * 10)()
@@ -333,6 +336,7 @@ class BatchContext(Context):
         self.riemannian = riemannian
         self.frobenius = frobenius
         self.K = sum(self.Ks)
+        self.blocks = self.K
         self.n_samples = sum(self.ns)
         self.n_circuits = nc
 

@@ -1,49 +1,39 @@
 """Translation-invariant brickwalls (App. E, Alg. 3): every gate of layer l
 is the same layer gate G_l, and the direction is layer-wise constant too.
 
-By the chain rule the derivatives with respect to a layer gate are the sums of
-the per-gate derivatives over the gates of that layer (App. E), for the
-gradient and the HVP alike; the Riemannian forms are linear in those sums for
-a fixed G_l, so they sum the same way. This wrapper expands layer gates to
-the per-gate arrays of a context and sums the results back per layer.
+The library does the work on the device (flag HVP_TRANSLATION): it expands
+the layer gates to every gate of their layer and sums the per-gate
+derivative blocks over each layer in FP64 (the chain rule through the tying
+map). This module only builds such a context and marshals (L, 4, 4) arrays.
 """
 from __future__ import annotations
 
-import numpy as np
-
-
-def layer_of_gates(n: int, n_layers: int) -> np.ndarray:
-    """Layer index (0-based) of every gate in the brickwall order."""
-    out = []
-    for layer in range(n_layers):
-        out += [layer] * ((n - layer % 2) // 2)
-    return np.array(out, dtype=np.int64)
-
-
-def expand(layer_gates, n: int, n_layers: int) -> np.ndarray:
-    """(L, 4, 4) layer gates -> (K, 4, 4) per-gate array."""
-    return np.asarray(layer_gates, dtype=np.complex128)[layer_of_gates(n, n_layers)]
-
-
-def contract(per_gate, n: int, n_layers: int) -> np.ndarray:
-    """(K, 4, 4) per-gate derivatives -> (L, 4, 4) sums over each layer."""
-    out = np.zeros((n_layers, 4, 4), dtype=np.complex128)
-    np.add.at(out, layer_of_gates(n, n_layers), np.asarray(per_gate))
-    return out
+from . import native
 
 
 class TranslationInvariant:
-    """Loss, gradient and HVP with respect to layer gates, on top of a
-    :class:`paper_2604_20384_gb300.native.Context` for the same brickwall."""
+    """Loss, gradient and HVP with respect to the L layer gates of a
+    brickwall; keyword arguments as for :class:`native.Context`."""
 
-    def __init__(self, ctx):
-        self.ctx = ctx
-        self.n, self.L = ctx.n, ctx.n_layers
+    def __init__(self, n: int, n_layers: int, psi1q, ref, **kw):
+        self.ctx = native.Context(n, n_layers, psi1q, ref, translation=True, **kw)
+        self.n, self.L = n, n_layers
 
     def loss_grad(self, Gl):
-        loss, g = self.ctx.loss_grad(expand(Gl, self.n, self.L))
-        return loss, contract(g, self.n, self.L)
+        return self.ctx.loss_grad(Gl)
 
     def hvp(self, Gl, Vl):
-        loss, g, h = self.ctx.hvp(expand(Gl, self.n, self.L), expand(Vl, self.n, self.L))
-        return loss, contract(g, self.n, self.L), contract(h, self.n, self.L)
+        return self.ctx.hvp(Gl, Vl)
+
+    def hvp_dev(self, Gl_ptr: int, Vl_ptr: int | None, loss_ptr: int | None, grad_ptr: int | None,
+                hvp_ptr: int | None):
+        self.ctx.hvp_dev(Gl_ptr, Vl_ptr, loss_ptr, grad_ptr, hvp_ptr)
+
+    def close(self):
+        self.ctx.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

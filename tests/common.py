@@ -82,3 +82,24 @@ def headline_oracle():
         phi, o = oracle_parallel(w)
         _HEADLINE.update(w=w, phi=phi, o=o)
     return _HEADLINE["w"], _HEADLINE["phi"], _HEADLINE["o"]
+
+
+def layer_of_gates(n: int, n_layers: int) -> np.ndarray:
+    """Layer index (0-based) of every gate in the brickwall order (the
+    convention of the library's header)."""
+    out = []
+    for layer in range(n_layers):
+        out += [layer] * ((n - layer % 2) // 2)
+    return np.array(out, dtype=np.int64)
+
+
+def expand(layer_gates, n: int, n_layers: int) -> np.ndarray:
+    """(L, 4, 4) layer gates -> (K, 4, 4), every gate of a layer the layer's."""
+    return np.asarray(layer_gates, dtype=np.complex128)[layer_of_gates(n, n_layers)]
+
+
+def contract(per_gate, n: int, n_layers: int) -> np.ndarray:
+    """(K, 4, 4) per-gate blocks -> (L, 4, 4) sums over each layer."""
+    out = np.zeros((n_layers, 4, 4), dtype=np.complex128)
+    np.add.at(out, layer_of_gates(n, n_layers), np.asarray(per_gate))
+    return out

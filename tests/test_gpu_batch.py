@@ -58,6 +58,21 @@ def test_batch_window_widths_and_autotune(window, autotune):
         assert rel(hvps[i], o["hvp"]) < TOL, (i, rel(hvps[i], o["hvp"]))
 
 
+@pytest.mark.parametrize("count", [1, 3])
+def test_odd_number_of_circuits(count):
+    # the per-gate result blocks start after one loss per circuit: with an odd
+    # count they must still be 16-byte aligned (double2 arrays)
+    ws, circuits = _small_batch()
+    ws, circuits = ws[:count], circuits[:count]
+    with native.BatchContext(circuits) as b:
+        loss, grads, hvps = b.hvp([w.G for w in ws], [w.V for w in ws])
+    for i, w in enumerate(ws):
+        phi = oracle.reference_states(w.n, w.n_layers, w.Uref, w.psi1q)
+        o = oracle.evaluate(w.n, w.n_layers, w.G, w.V, w.psi1q, phi)
+        assert abs((1 - loss[i]) - (1 - o["loss"])) <= TOL * (1 - o["loss"]) + 1e-13, i
+        assert rel(grads[i], o["grad"]) < TOL and rel(hvps[i], o["hvp"]) < TOL
+
+
 def test_expired_chain_wait_is_reported_and_context_stays_usable():
     # every chain wait asks for a phase that never finishes: the first wait
     # gives up after 10^4 sleeps of 200 ns, the call reports HVP_ETIMEOUT, and

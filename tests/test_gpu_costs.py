@@ -4,11 +4,11 @@
 import numpy as np
 import pytest
 
-from common import rel
+from common import contract, expand, rel
 from oracle import oracle
 from paper_2604_20384_gb300 import native
 from paper_2604_20384_gb300.inputs import make_workload
-from paper_2604_20384_gb300.translation import TranslationInvariant, contract, expand
+from paper_2604_20384_gb300.translation import TranslationInvariant
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -39,18 +39,37 @@ def test_frobenius_cost_in_a_batch():
         assert rel(gs[i], o["grad_f"]) < TOL and rel(hs[i], o["hvp_f"]) < TOL
 
 
-def test_translation_invariant_layers_match_oracle():
+@pytest.mark.parametrize("kw", [dict(window=10), dict(tensor=True), dict(riemannian=True), dict(recompute=True),
+                                dict(unfused=True, precision="c128")])
+def test_translation_invariant_layers_match_oracle(kw):
+    # App. E on the device (HVP_TRANSLATION): layer gates expanded to every gate,
+    # per-gate blocks summed per layer in FP64; host arrays and device pointers
+    torch = pytest.importorskip("torch")
     n, L, ns = 13, 7, 6
     w = make_workload(n, L, ns, seed=81)
     first = np.cumsum([0] + [(n - l % 2) // 2 for l in range(L)])[:-1]
     Gl, Vl = w.G[first], w.V[first]
     phi = oracle.reference_states(n, L, w.Uref, w.psi1q)
     o = oracle.evaluate(n, L, expand(Gl, n, L), expand(Vl, n, L), w.psi1q, phi)
-    with native.Context(n, L, w.psi1q, w.Uref, window=10) as c:
-        loss, g, h = TranslationInvariant(c).hvp(Gl, Vl)
-    assert abs(loss - o["loss"]) < TOL
-    assert rel(g, contract(o["grad"], n, L)) < TOL
-    assert rel(h, contract(o["hvp"], n, L)) < TOL
+    tol = 1e-11 if kw.get("precision") == "c128" else TOL
+    kg, kh = ("grad_r", "hvp_r") if kw.get("riemannian") else ("grad", "hvp")
+    with TranslationInvariant(n, L, w.psi1q, w.Uref, **kw) as ti:
+        loss, g, h = ti.hvp(Gl, Vl)
+        assert abs(loss - o["loss"]) < tol
+        assert rel(g, contract(o[kg], n, L)) < tol
+        assert rel(h, contract(o[kh], n, L)) < tol
+        loss2, g2 = ti.loss_grad(Gl)
+        assert rel(g2, contract(o[kg], n, L)) < tol
+        dev = torch.device("cuda", 0)
+        Gd = torch.from_numpy(np.ascontiguousarray(Gl).view(np.float64).reshape(-1).copy()).to(dev)
+        Vd = torch.from_numpy(np.ascontiguousarray(Vl).view(np.float64).reshape(-1).copy()).to(dev)
+        gd = torch.zeros(32 * L, dtype=torch.float64, device=dev)
+        hd = torch.zeros(32 * L, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        ti.hvp_dev(Gd.data_ptr(), Vd.data_ptr(), None, gd.data_ptr(), hd.data_ptr())
+        torch.cuda.synchronize()
+        assert rel(gd.cpu().numpy().view(np.complex128).reshape(L, 4, 4), contract(o[kg], n, L)) < tol
+        assert rel(hd.cpu().numpy().view(np.complex128).reshape(L, 4, 4), contract(o[kh], n, L)) < tol
 
 
 def test_dense_riemannian_hessian_spectrum_on_gpu():

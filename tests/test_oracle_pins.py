@@ -422,7 +422,7 @@ def test_frobenius_riemannian_hessian_self_adjoint():
 def test_translation_invariant_chain_rule():
     # Layer-gate derivatives are the per-gate sums over the layer (App. E):
     # checked against central differences in the layer gates themselves.
-    from paper_2604_20384_gb300.translation import contract, expand
+    from common import contract, expand
 
     n, L, ns = 6, 4, 5
     w = make_workload(n, L, ns, seed=51)
