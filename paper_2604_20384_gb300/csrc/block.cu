@@ -8,10 +8,11 @@
 //     B = G_m ... G_1,      dB = sum_i G_m .. V_i .. G_1      (App. D: the
 // tangent of a product is the block-triangular operator [[B, 0], [dB, B]]).
 // The tensor-core passes apply [[B, 0], [dB, B]] forward to (psi, dpsi) and
-// [[B^dag, 0], [dB^dag, B^dag]] backward to the co-states, both as real
-// 128 x 128 operators on the interleaved components (re psi, im psi,
-// re dpsi, im dpsi) of the 32 block amplitudes, stored as three slices of
-// 8-bit integers per row (see internal.h).
+// [[B^dag, 0], [dB^dag, B^dag]] backward to the co-states (c, dc) as one real
+// GEMM per tile: the 128 x 64 operator B over dB times the columns psi | dpsi
+// gives B psi, B dpsi over dB psi, dB dpsi, of which psi' = B psi and dpsi' =
+// B dpsi + dB psi are read (likewise backward). The operator is stored as
+// three slices of 8-bit integers per row (see internal.h).
 //
 // Block environments. The backward pass accumulates, over every amplitude
 // of every sample, P[4a + p][4b + q] = sum C_p[a] Psi_q[b], where C = (re c,
@@ -56,15 +57,10 @@ __device__ __forceinline__ void gate_rows(int x, int hb, int (&r)[4]) {
     r[3] = r0 | (1 << hb) | (1 << lb);
 }
 
-// Real embedding of [[X, 0], [dX, X]] on the interleaved components: row
-// 4b' + p', column 4b + p (p = re, im of the state, re, im of the tangent).
-__device__ __forceinline__ double embed(int pr, int pc, double2 x, double2 dx) {
-    switch (pr) {
-        case 0: return pc == 0 ? x.x : pc == 1 ? -x.y : 0.0;
-        case 1: return pc == 0 ? x.y : pc == 1 ? x.x : 0.0;
-        case 2: return pc == 0 ? dx.x : pc == 1 ? -dx.y : pc == 2 ? x.x : -x.y;
-        default: return pc == 0 ? dx.y : pc == 1 ? dx.x : pc == 2 ? x.y : x.x;
-    }
+// Real embedding of a complex entry x: output component qr (re, im) from
+// input component qc (re, im).
+__device__ __forceinline__ double embed(int qr, int qc, double2 x) {
+    return qr == 0 ? (qc == 0 ? x.x : -x.y) : (qc == 0 ? x.y : x.x);
 }
 
 // bf16 bits of an integer of magnitude <= 256 (exact).
@@ -72,7 +68,7 @@ __device__ __forceinline__ uint32_t bf16_int(double v) { return __float_as_uint(
 
 // One CTA per block (256 threads): B and dB by applying the block's gates to
 // the identity, then the block's operator record (see internal.h): for each
-// direction and half, each of the 128 rows is split into three slices of
+// direction, each of the 128 rows (B over dB) is split into three slices of
 // 8-bit integers on a common power-of-two row scale, so that the tensor-core
 // products of slices and their sums over K = 64 are exact integers in FP32.
 __global__ void __launch_bounds__(256) block_prep_kernel(const DevBlock* __restrict__ blocks,
@@ -121,15 +117,16 @@ __global__ void __launch_bounds__(256) block_prep_kernel(const DevBlock* __restr
     __syncthreads();
     uint32_t* o = ops + (size_t)blockIdx.x * kOpWords;
     float* scales = reinterpret_cast<float*>(o + kOpScaleOff);
-    // 512 (direction, half, row) lines, two per thread: row entries K = 2 b + q
-    // (q = re, im of the half's input components).
-    for (int line = t; line < 512; line += 256) {
-        const int d = line >> 8, h = (line >> 7) & 1, row = line & 127, b1 = row >> 2, p1 = row & 3;
+    // 256 (direction, row) lines, one per thread: rows 2 b' + q of X (B or
+    // B^dag), then 64 + 2 b' + q of dX; entries K = 2 b + (re, im).
+    {
+        const int line = t, d = line >> 7, row = line & 127, b1 = (row & 63) >> 1, q1 = row & 1;
+        const bool drow = row >= 64;
         auto entry = [&](int k) {
-            const int b0 = k >> 1, p0 = (k & 1) + 2 * h;
-            const double2 xv = d ? zconj(M[b0 * 32 + b1]) : M[b1 * 32 + b0];
-            const double2 dxv = d ? zconj(dM[b0 * 32 + b1]) : dM[b1 * 32 + b0];
-            return embed(p1, p0, xv, dxv);
+            const int b0 = k >> 1;
+            const double2 m = drow ? (d ? zconj(dM[b0 * 32 + b1]) : dM[b1 * 32 + b0])
+                                   : (d ? zconj(M[b0 * 32 + b1]) : M[b1 * 32 + b0]);
+            return embed(q1, k & 1, m);
         };
         double amax = 0.0;
         for (int k = 0; k < 64; ++k) {
@@ -140,22 +137,22 @@ __global__ void __launch_bounds__(256) block_prep_kernel(const DevBlock* __restr
         int f = 0;
         if (amax > 0.0 && isfinite(amax)) frexp(amax, &f);   // 2^f > amax >= 2^(f-1)
         const double up = ldexp(1.0, 8 - f);
-        scales[(d * 2 + h) * 128 + row] = (float)ldexp(1.0, f - 8);
-        uint32_t* s0 = o + ((d * 2 + h) * 3 + 0) * kOpSliceWords + row * 32;
+        scales[d * 128 + row] = (float)ldexp(1.0, f - 8);
+        uint32_t* s0 = o + (d * 3 + 0) * kOpSliceWords + row * 32;
         uint32_t* s1 = s0 + kOpSliceWords;
         uint32_t* s2 = s1 + kOpSliceWords;
         for (int w = 0; w < 32; ++w) {
-            uint32_t q0 = 0, q1 = 0, q2 = 0;
+            uint32_t q0 = 0, qa = 0, qb = 0;
             for (int hlf = 0; hlf < 2; ++hlf) {
                 const double y = isfinite(amax) ? entry(2 * w + hlf) * up : 0.0;
                 const double a0 = rint(y), y1 = (y - a0) * 256.0, a1 = rint(y1), a2 = rint((y1 - a1) * 256.0);
                 q0 |= bf16_int(a0) << (16 * hlf);
-                q1 |= bf16_int(a1) << (16 * hlf);
-                q2 |= bf16_int(a2) << (16 * hlf);
+                qa |= bf16_int(a1) << (16 * hlf);
+                qb |= bf16_int(a2) << (16 * hlf);
             }
             s0[w] = q0;
-            s1[w] = q1;
-            s2[w] = q2;
+            s1[w] = qa;
+            s2[w] = qb;
         }
     }
     if (!ok) atomicOr(status, 1);

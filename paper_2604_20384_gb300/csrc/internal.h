@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libhvp.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -117,16 +118,16 @@ enum TcbMode : int {
 };
 
 // Operator record of one block (kOpWords 32-bit words). For direction d (0
-// forward [[B, 0], [dB, B]], 1 backward [[B^dag, 0], [dB^dag, B^dag]]) and
-// half h (0: the operator's columns acting on the state components, 1: on the
-// tangent components), slice i = 0, 1, 2: 128 rows x 32 words, each word two
-// bf16 integers in [-256, 256] (K elements 2w in the low half, 2w + 1 in the
-// high half; K = 2 b + (re, im)); then the row scales [d][h][128] as floats.
-// Row m of half h is scale * (s_0 + s_1 / 256 + s_2 / 65536) exactly up to
-// 2^-25 of the row's largest entry.
+// forward: B over dB, 1 backward: B^dag over dB^dag), the real 128 x 64
+// operator whose rows 2 b' + q (q = re, im) are those of B and rows
+// 64 + 2 b' + q those of dB, acting on K = 2 b + (re, im) of 32 block
+// amplitudes. Slice i = 0, 1, 2: 128 rows x 32 words, each word two bf16
+// integers in [-256, 256] (K element 2w in the low half, 2w + 1 in the high
+// half); then the row scales [d][128] as floats. Row m is scale * (s_0 + s_1 /
+// 256 + s_2 / 65536) exactly up to 2^-25 of the row's largest entry.
 constexpr int kOpSliceWords = 128 * 32;
-constexpr int kOpScaleOff = 2 * 2 * 3 * kOpSliceWords;
-constexpr int kOpWords = kOpScaleOff + 2 * 2 * 128;
+constexpr int kOpScaleOff = 2 * 3 * kOpSliceWords;
+constexpr int kOpWords = kOpScaleOff + 2 * 128;
 
 struct TcbArgs {
     const uint32_t* ops;     // this block's operator record (kOpWords words)
@@ -144,6 +145,12 @@ struct TcbArgs {
     unsigned wait_limit;     // polls before a wait gives up (0: the default)
     unsigned barrier_extra;  // test of the bounded waits: arrivals the tile barriers expect beyond the
                              // MMAs' commit (0 in normal use)
+    // Tensor maps of xin and psi for the TMA tile loads, and whether each is
+    // used (written by launch_tcb from the fields above; without a map the
+    // threads load their elements directly).
+    int tma_x, tma_p;
+    CUtensorMap tm_x;
+    CUtensorMap tm_p;
 };
 cudaError_t launch_tcb(const TcbArgs& a, bool bwd, int ctas, cudaStream_t st);
 cudaError_t tcb_set_smem_limits();
