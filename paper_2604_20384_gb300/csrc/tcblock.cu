@@ -65,6 +65,7 @@ constexpr unsigned kSumCol = kEnvCol + 128;      // backward: FP32 running sums 
                                                  //   16..63 of each producer thread's 64 (96 columns)
 constexpr int kFlushTiles = 16;              // FP32 tiles summed before an FP64 flush
 constexpr unsigned kWaitLimit = 1u << 22;    // mbarrier polls before a wait gives up
+constexpr unsigned kSettleLimit = 1u << 16;  // polls for an outstanding copy on the way out
 
 // X slices: K = 64 x NE columns, bf16, K-major core matrices (8 columns x 16
 // bytes). K-cores 144 bytes apart (a 16-byte gap, so that a warp's 4-byte
@@ -83,6 +84,7 @@ constexpr unsigned kERegion = 16 * kSboE;         // one TF32 part (high or low)
 // one column hit distinct bank groups).
 constexpr unsigned kRowF4 = 33;
 constexpr unsigned kStagingBytes = 32 * kRowF4 * 16;
+constexpr unsigned kStaging2Bytes = 32 * kRowF4 * 8;   // dB psi (dB^dag c): float2 per (block index, column)
 // Ring of raw input tiles filled by TMA tile loads: forward 4 tiles of X;
 // backward 2 of X (co-states) and 2 of the forward states Psi, so that
 // several tiles' loads are in flight per SM. A raw tile is four 4 KB boxes
@@ -119,7 +121,8 @@ __host__ __device__ constexpr unsigned off_x(bool bwd) { return (unsigned)(ring_
 __host__ __device__ constexpr unsigned off_psi(bool bwd) { return off_x(bwd) + 2 * kXSlot; }
 __host__ __device__ constexpr unsigned off_dbuf(bool bwd) { return off_psi(bwd) + (bwd ? 2 * kERegion : 0u); }
 __host__ __device__ constexpr unsigned off_stg(bool bwd) { return off_dbuf(bwd) + (bwd ? 2 * kERegion : 0u); }
-__host__ __device__ constexpr unsigned off_csc(bool bwd) { return off_stg(bwd) + kStagingBytes; }
+__host__ __device__ constexpr unsigned off_stg2(bool bwd) { return off_stg(bwd) + kStagingBytes; }
+__host__ __device__ constexpr unsigned off_csc(bool bwd) { return off_stg2(bwd) + kStaging2Bytes; }
 __host__ __device__ constexpr unsigned off_bars(bool bwd) { return off_csc(bwd) + 4 * NE * 4; }
 __host__ __device__ constexpr unsigned smem_bytes(bool bwd) { return off_bars(bwd) + B_COUNT * 8 + 16 + 1024; }
 // Dynamic shared memory of a launch: at least 116 KB, so that one CTA runs
@@ -265,9 +268,6 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int 
             "r"(smem_u32(bar))
             : "memory");
 }
-__device__ __forceinline__ void red_add_smem(float* p, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_u32(p)), "f"(v) : "memory");
-}
 // Barriers of one role's 256 threads (id 1: producers, id 2: epilogue); the
 // second returns the OR of every participant's flag, the same in every thread.
 __device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
     unsigned char* psislots = base + off_psi(BWD);
     unsigned char* dbuf = base + off_dbuf(BWD);
     float* staging = reinterpret_cast<float*>(base + off_stg(BWD));
+    float* staging2 = reinterpret_cast<float*>(base + off_stg2(BWD));
     float* csc = reinterpret_cast<float*>(base + off_csc(BWD));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + off_bars(BWD));
     volatile unsigned* ctl = reinterpret_cast<volatile unsigned*>(bars + B_COUNT);   // [TMEM base, stop]
@@ -406,6 +407,109 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         return false;
     };
 
+    // ------------------------------------------------------------ input ring
+    // Used by the producers (X) and, backward, by the epilogue (Psi): a
+    // worker thread's elements are block index lane, columns 4 qd .. 4 qd + 3
+    // (qd its warp's column quad); the role's first thread issues the TMA
+    // loads.
+    const int qd = warp < 8 ? warp : warp - 8;
+    const bool leader = tid == 0 || tid == 256;
+    bool bad = false;
+    // Raw tiles: four 4 KB boxes of 8 columns (c = 8 g + c'). Block bits at
+    // bl >= 3: box g row b = the 8 columns of block index b (128 bytes,
+    // 16-byte chunk c' XOR (b mod 8), the TMA's 128-byte swizzle); bl < 3:
+    // box g holds 8 / 2^bl runs of 32 x 2^bl amplitudes in memory order.
+    // Either way the 32 block indices of one column are conflict-free
+    // for bl = 0 and bl >= 3 (2- and 4-way at bl = 1, 2).
+    auto tile_off = [&](unsigned b, unsigned c) -> unsigned {
+        const unsigned g = c >> 3, cq = c & 7u;
+        if (bl >= 3) return g * 4096u + b * 128u + ((cq ^ (b & 7u)) << 4);
+        const unsigned pl = 1u << bl;
+        return g * 4096u + (((cq >> bl) * 32u + b) * pl + (cq & (pl - 1u))) * 16u;
+    };
+    // Loads of local tile j (global tile blockIdx.x + j gridDim.x) into
+    // ring slot s: one thread issues the four TMA box loads (expecting
+    // their bytes on the slot's barrier); computed inputs (product states,
+    // weighted reference states), and inputs without a tensor map, are
+    // loaded or computed by every thread for its own elements instead,
+    // each arriving on the barrier. Nothing is issued for tiles past the
+    // end (no one waits for them).
+    long long x_issued = 0, x_taken = 0, p_issued = 0, p_taken = 0;   // local tiles
+    auto issue = [&](long long j, int s, bool psi) {
+        const long long tile = (long long)blockIdx.x + j * g;
+        if (tile >= ntiles) return;
+        (psi ? p_issued : x_issued) = j + 1;
+        unsigned char* dst = ring + (unsigned)s * kRawTile;
+        const bool gen = psi ? (a.mode & TCB_GEN) != 0
+                             : (!BWD && (a.mode & TCB_GEN)) || (BWD && (a.mode & TCB_LOAD_PHI));
+        const long long c0 = tile * TN;
+        if (!gen && (psi ? a.tma_p : a.tma_x)) {
+            if (leader) {   // (the role's reads of the slot precede its barrier before this refill)
+                mbar_arrive_expect_tx(&bars[B_RING0 + s], kRawTile);
+                const CUtensorMap* map = psi ? &a.tm_p : &a.tm_x;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const long long cg = c0 + 8 * q;
+                    if (bl >= 3)
+                        tma_load(dst + 4096 * q, map, 0, (int)((cg & ((1ll << bl) - 1)) >> 3), 0, (int)(cg >> bl),
+                                 &bars[B_RING0 + s], true);
+                    else
+                        tma_load(dst + 4096 * q, map, 0, 0, (int)(cg >> bl), 0, &bars[B_RING0 + s], false);
+                }
+            }
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const unsigned c = (unsigned)(4 * qd + i);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c0 + c < ncols) {
+                const size_t gi = amp_index(c0 + c, (unsigned)lane, bl);
+                if (!gen) {
+                    v = __ldcs((psi ? a.psi : a.xin) + gi);
+                } else if (psi || !BWD) {
+                    const float2 p = product_amp(a.psi1q, gi, n);
+                    v = make_float4(p.x, p.y, 0.f, 0.f);
+                } else {
+                    const float2 ph = __ldg(&a.phi[gi]);
+                    const size_t smp = gi >> n;
+                    float2 w1 = make_float2(1.f, 0.f), w2 = make_float2(0.f, 0.f);
+                    if (a.w1) w1 = make_float2((float)a.w1[smp].x, (float)a.w1[smp].y);
+                    if (a.w2) w2 = make_float2((float)a.w2[smp].x, (float)a.w2[smp].y);
+                    v = make_float4(w1.x * ph.x - w1.y * ph.y, w1.x * ph.y + w1.y * ph.x,
+                                    w2.x * ph.x - w2.y * ph.y, w2.x * ph.y + w2.y * ph.x);
+                }
+            }
+            *reinterpret_cast<float4*>(dst + tile_off((unsigned)lane, c)) = v;
+        }
+        mbar_arrive(&bars[B_RING0 + s]);   // (release: orders the stores above)
+    };
+    auto issue_x = [&](long long j) { issue(j, (int)(j % RX), false); };
+    auto issue_p = [&](long long j) { issue(j, RX + (int)(j % (RP > 0 ? RP : 1)), true); };
+    // The thread's four raw values of local tile j (zero past the last
+    // column), once the slot is full.
+    auto take = [&](long long j, int s, int uses, bool psi, float4 (&v)[4]) {
+        if (wait(B_RING0 + s, (unsigned)(uses & 1))) (psi ? p_taken : x_taken) = j + 1;
+        else bad = true;
+        const unsigned char* src = ring + (unsigned)s * kRawTile;
+        const long long c0 = ((long long)blockIdx.x + j * g) * TN;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const unsigned c = (unsigned)(4 * qd + i);
+            v[i] = *reinterpret_cast<const float4*>(src + tile_off((unsigned)lane, c));
+            if (c0 + c >= ncols) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!tangent) { v[i].z = 0.f; v[i].w = 0.f; }
+        }
+    };
+    // No copy into shared memory outlives the CTA: after a failed wait,
+    // tiles issued but not taken are waited for (bounded, regardless of the
+    // stop flag).
+    auto settle = [&](long long from, long long to, int base, int depth) {
+        for (long long q = from; q < to; ++q)
+            for (unsigned k = 0; k < kSettleLimit; ++k)
+                if (mbar_try(&bars[B_RING0 + base + (int)(q % depth)], (unsigned)((q / depth) & 1))) break;
+    };
+
     if (mma_warp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -472,95 +576,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         // the block index b = l: column maxima are warp reductions.
         const unsigned ub = (unsigned)lane;
         const int uq = warp;
-        bool bad = false, ok = true;
-        // Raw tiles: four 4 KB boxes of 8 columns (c = 8 g + c'). Block bits at
-        // bl >= 3: box g row b = the 8 columns of block index b (128 bytes,
-        // 16-byte chunk c' XOR (b mod 8), the TMA's 128-byte swizzle); bl < 3:
-        // box g holds 8 / 2^bl runs of 32 x 2^bl amplitudes in memory order.
-        // Either way the 32 block indices of one column are conflict-free
-        // for bl = 0 and bl >= 3 (2- and 4-way at bl = 1, 2).
-        auto tile_off = [&](unsigned b, unsigned c) -> unsigned {
-            const unsigned g = c >> 3, cq = c & 7u;
-            if (bl >= 3) return g * 4096u + b * 128u + ((cq ^ (b & 7u)) << 4);
-            const unsigned pl = 1u << bl;
-            return g * 4096u + (((cq >> bl) * 32u + b) * pl + (cq & (pl - 1u))) * 16u;
-        };
-        // Loads of local tile j (global tile blockIdx.x + j gridDim.x) into
-        // ring slot s: one thread issues the four TMA box loads (expecting
-        // their bytes on the slot's barrier); computed inputs (product states,
-        // weighted reference states), and inputs without a tensor map, are
-        // loaded or computed by every thread for its own elements instead,
-        // each arriving on the barrier. Nothing is issued for tiles past the
-        // end (no one waits for them).
-        long long x_issued = 0, x_taken = 0, p_issued = 0, p_taken = 0;   // local tiles
-        auto issue = [&](long long j, int s, bool psi) {
-            const long long tile = (long long)blockIdx.x + j * g;
-            if (tile >= ntiles) return;
-            (psi ? p_issued : x_issued) = j + 1;
-            unsigned char* dst = ring + (unsigned)s * kRawTile;
-            const bool gen = psi ? (a.mode & TCB_GEN) != 0
-                                 : (!BWD && (a.mode & TCB_GEN)) || (BWD && (a.mode & TCB_LOAD_PHI));
-            const long long c0 = tile * TN;
-            if (!gen && (psi ? a.tma_p : a.tma_x)) {
-                if (tid == 0) {
-                    fence_async_smem();   // the producers' reads of the slot come first
-                    mbar_arrive_expect_tx(&bars[B_RING0 + s], kRawTile);
-                    const CUtensorMap* map = psi ? &a.tm_p : &a.tm_x;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const long long cg = c0 + 8 * q;
-                        if (bl >= 3)
-                            tma_load(dst + 4096 * q, map, 0, (int)((cg & ((1ll << bl) - 1)) >> 3), 0, (int)(cg >> bl),
-                                     &bars[B_RING0 + s], true);
-                        else
-                            tma_load(dst + 4096 * q, map, 0, 0, (int)(cg >> bl), 0, &bars[B_RING0 + s], false);
-                    }
-                }
-                return;
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const unsigned c = (unsigned)(4 * uq + i);
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (c0 + c < ncols) {
-                    const size_t gi = amp_index(c0 + c, ub, bl);
-                    if (!gen) {
-                        v = __ldcs((psi ? a.psi : a.xin) + gi);
-                    } else if (psi || !BWD) {
-                        const float2 p = product_amp(a.psi1q, gi, n);
-                        v = make_float4(p.x, p.y, 0.f, 0.f);
-                    } else {
-                        const float2 ph = __ldg(&a.phi[gi]);
-                        const size_t smp = gi >> n;
-                        float2 w1 = make_float2(1.f, 0.f), w2 = make_float2(0.f, 0.f);
-                        if (a.w1) w1 = make_float2((float)a.w1[smp].x, (float)a.w1[smp].y);
-                        if (a.w2) w2 = make_float2((float)a.w2[smp].x, (float)a.w2[smp].y);
-                        v = make_float4(w1.x * ph.x - w1.y * ph.y, w1.x * ph.y + w1.y * ph.x,
-                                        w2.x * ph.x - w2.y * ph.y, w2.x * ph.y + w2.y * ph.x);
-                    }
-                }
-                *reinterpret_cast<float4*>(dst + tile_off(ub, c)) = v;
-            }
-            mbar_arrive(&bars[B_RING0 + s]);   // (release: orders the stores above)
-        };
-        auto issue_x = [&](long long j) { issue(j, (int)(j % RX), false); };
-        auto issue_p = [&](long long j) { issue(j, RX + (int)(j % (RP > 0 ? RP : 1)), true); };
-        // The thread's four raw values of local tile j (zero past the last
-        // column), once the slot is full.
-        auto take = [&](long long j, int s, int uses, bool psi, float4 (&v)[4]) {
-            if (wait(B_RING0 + s, (unsigned)(uses & 1))) (psi ? p_taken : x_taken) = j + 1;
-            else bad = true;
-            const unsigned char* src = ring + (unsigned)s * kRawTile;
-            const long long c0 = ((long long)blockIdx.x + j * g) * TN;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const unsigned c = (unsigned)(4 * uq + i);
-                v[i] = *reinterpret_cast<const float4*>(src + tile_off(ub, c));
-                if (c0 + c >= ncols) v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!tangent) { v[i].z = 0.f; v[i].w = 0.f; }
-            }
-            fence_async_smem();   // these reads come before the slot's next fill
-        };
+        bool ok = true;
         // Local tile j -> X slot sg: per column (state and tangent part) the
         // scale exponent from the warp maximum (published in scale slot j mod
         // 4), then the slices. (The ring slot is refilled once every producer
@@ -602,31 +618,6 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             fence_async_smem();
             mbar_arrive(&bars[B_FULL0 + sg]);
         };
-        // Backward: the forward states of local tile j as the TF32 operand of
-        // the environment GEMM (rows 4 b + p, 4 columns per 16-byte row; high
-        // and low parts).
-        auto produce_psi = [&](long long j) {
-            if constexpr (BWD) {
-                float4 v[4];
-                take(j, RX + (int)(j % RP), (int)(j / RP), true, v);
-                const unsigned base = (unsigned)uq * kLboE + (ub >> 1) * kSboE + (ub & 1u) * 64u;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float h[4], l[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float x = p == 0 ? v[i].x : p == 1 ? v[i].y : p == 2 ? v[i].z : v[i].w;
-                        h[i] = tf32_rna(x);
-                        l[i] = tf32_rna(x - h[i]);
-                    }
-                    *reinterpret_cast<float4*>(psislots + base + 16 * p) = make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4*>(psislots + kERegion + base + 16 * p) =
-                        make_float4(l[0], l[1], l[2], l[3]);
-                }
-                fence_async_smem();
-            }
-        };
-
         // Backward: FP32 running sums of the environment, this thread's TMEM
         // lane (row 4 b + p of D) and columns 64 k .. 64 k + 63 (k = w / 4,
         // rows of Psi): the first 16 in registers, the other 48 in TMEM.
@@ -697,12 +688,11 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         // Producers run one tile ahead: in iteration j they stage X of tile
         // j + 1 (its slot is free once the update MMAs of tile j - 1 are
         // done), then (backward) read the environment of tile j - 1, which
-        // the tensor pipe ran after the update of tile j, and stage the
-        // forward states of tile j.
+        // the tensor pipe ran after the update of tile j, so that the
+        // environment of tile j may follow.
         long long j = 0;
         if ((long long)blockIdx.x < ntiles) {
             for (int q = 0; q < RX; ++q) issue_x(q);
-            for (int q = 0; q < RP; ++q) issue_p(q);
             produce_x(0, 0);
         }
         if (group_sync_or(1, bad)) ok = false;
@@ -720,7 +710,6 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                     tc_fence_after();
                     read_env();
                 }
-                produce_psi(j);
                 tc_fence_before();
                 mbar_arrive(&bars[B_PREADY]);
             }
@@ -728,7 +717,6 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             // read the ring slots taken above: refill them
             if (group_sync_or(1, bad)) { ok = false; break; }
             if (more) issue_x(j + 1 + RX);
-            if (BWD) issue_p(j + RP);
         }
         if (BWD && ok && j > 0) {   // the last tile's environment
             if (!wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
@@ -740,16 +728,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             }
         }
         if (ok && BWD && (since_flush > 0 || !flushed)) flush();
-        // No copy into shared memory outlives the CTA: after a failed wait,
-        // tiles issued but not taken are waited for (bounded, regardless of
-        // the stop flag).
-        auto settle = [&](long long from, long long to, int base, int depth) {
-            for (long long q = from; q < to; ++q)
-                for (unsigned k = 0; k < kWaitLimit; ++k)
-                    if (mbar_try(&bars[B_RING0 + base + (int)(q % depth)], (unsigned)((q / depth) & 1))) break;
-        };
         settle(x_taken, x_issued, 0, RX);
-        if (RP > 0) settle(p_taken, p_issued, RX, RP > 0 ? RP : 1);
     } else {
         // ------------------------------------------------------------ epilogue
         // Thread = TMEM lane = operator row. Rows 0-63 (warps with w % 4 < 2)
@@ -759,7 +738,6 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         // columns per warp: B rows 32 (state part for e = w - 8 < 4, tangent
         // part for e >= 4), dB rows 16.
         const int e = warp - 8;
-        bool bad = false;
         const float rs = __ldg(reinterpret_cast<const float*>(a.ops + kOpScaleOff) + dir * 128 + row);
         const bool brow = (warp & 3) < 2;
         const int nchunk = tangent ? (brow ? 2 : 1) : (brow ? 1 : 0);
@@ -781,9 +759,9 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 }
             }
         };
-        // Staging: float4 of (block index b, column c) at b * 33 + c. B rows
-        // store psi' and B dpsi; dB rows add dB psi to the tangent part once
-        // those are in place.
+        // Staging: float4 of (block index b, column c) at b * 33 + c (B rows:
+        // psi' and B dpsi), float2 at b * 33 + c (dB rows: dB psi), added
+        // when the tile is read.
         auto put = [&](int cb, const float (&v)[16]) {
             const unsigned p = (cb >= TN ? 2u : 0u) + qc;
 #pragma unroll
@@ -793,12 +771,49 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 if (!tangent) staging[((bq * kRowF4 + c) << 2) + 2 + qc] = 0.f;
             }
         };
-        auto add_dB = [&](int cb, const float (&v)[16]) {
+        auto put_dB = [&](int cb, const float (&v)[16]) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) red_add_smem(&staging[((bq * kRowF4 + (unsigned)(cb + k)) << 2) + 2 + qc], v[k]);
+            for (int k = 0; k < 16; ++k) staging2[((bq * kRowF4 + (unsigned)(cb + k)) << 1) + qc] = v[k];
         };
         const float4* st4 = reinterpret_cast<const float4*>(staging);
+        const float2* st2 = reinterpret_cast<const float2*>(staging2);
+        auto out = [&](unsigned b, unsigned c) {
+            float4 o = st4[b * kRowF4 + c];
+            if (tangent) {
+                const float2 d = st2[b * kRowF4 + c];
+                o.z += d.x;
+                o.w += d.y;
+            }
+            return o;
+        };
 
+        // Backward: the forward states of local tile j as the TF32 operand of
+        // the environment GEMM (rows 4 b + p, 4 columns per 16-byte row; high
+        // and low parts).
+        auto produce_psi = [&](long long j) {
+            if constexpr (BWD) {
+                float4 v[4];
+                take(j, RX + (int)(j % RP), (int)(j / RP), true, v);
+                const unsigned base = (unsigned)qd * kLboE + ((unsigned)lane >> 1) * kSboE + ((unsigned)lane & 1u) * 64u;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    float h[4], l[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float x = p == 0 ? v[i].x : p == 1 ? v[i].y : p == 2 ? v[i].z : v[i].w;
+                        h[i] = tf32_rna(x);
+                        l[i] = tf32_rna(x - h[i]);
+                    }
+                    *reinterpret_cast<float4*>(psislots + base + 16 * p) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(psislots + kERegion + base + 16 * p) =
+                        make_float4(l[0], l[1], l[2], l[3]);
+                }
+                fence_async_smem();
+            }
+        };
+
+        if (BWD && (long long)blockIdx.x < ntiles)
+            for (int q = 0; q < RP; ++q) issue_p(q);
         long long j = 0;
         for (long long tile = blockIdx.x; tile < ntiles; tile += g, ++j) {
             const int ab = NB == 2 ? (int)(j & 1) : 0;
@@ -816,12 +831,12 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 if (nchunk > 0) combine(accb, cb0 + (nchunk - 1) * 16, cs, v);
                 tc_fence_before();
                 mbar_arrive(&bars[B_FREE0 + ab]);
-                if (nchunk > 0 && brow) put(cb0 + (nchunk - 1) * 16, v);
+                if (nchunk > 0) {
+                    if (brow) put(cb0 + (nchunk - 1) * 16, v);
+                    else put_dB(cb0, v);
+                }
             }
             if (group_sync_or(2, bad)) break;
-            if (nchunk > 0 && !brow) add_dB(cb0, v);
-            fence_async_smem();
-            group_sync(2);
             // staging -> global in memory order (consecutive lanes, 512
             // contiguous bytes per warp instruction for bl >= 5)
             const long long c0 = tile * TN;
@@ -831,7 +846,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 for (int k = 0; k < 4; ++k) {
                     const unsigned f = (unsigned)(32 * (4 * e + k) + lane);
                     const unsigned c = (f & bmk) | ((f >> (bm + 5)) << bm), b = (f >> bm) & 31u;
-                    if (c0 + c < ncols) __stcs(&a.xout[amp_index(c0 + c, b, bl)], st4[b * kRowF4 + c]);
+                    if (c0 + c < ncols) __stcs(&a.xout[amp_index(c0 + c, b, bl)], out(b, c));
                 }
             }
             if constexpr (BWD) {
@@ -842,7 +857,8 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 const unsigned base = (unsigned)e * kLboE + (ub >> 1) * kSboE + (ub & 1u) * 64u;
                 float4 o[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = st4[ub * kRowF4 + (unsigned)(4 * e + k)];
+                for (int k = 0; k < 4; ++k) o[k] = out(ub, (unsigned)(4 * e + k));
+                produce_psi(j);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     float h[4], l[4];
@@ -859,7 +875,9 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 mbar_arrive(&bars[B_CREADY]);
             }
             group_sync(2);   // the staging tile is reused by the next tile
+            if (BWD && !bad) issue_p(j + RP);   // every epilogue thread has read its forward states
         }
+        if (BWD) settle(p_taken, p_issued, RX, RP > 0 ? RP : 1);
     }
     tc_fence_before();
     __syncthreads();
