@@ -328,6 +328,72 @@ def n26_autograd_line(make_workload, torch, dev, local) -> dict:
             "device_mib": info["device_mib"]}
 
 
+def tensor_line(native, torch, dev, local, w, steps: int, m: int):
+    """The same workload on the fused-block tensor-core schedule (HVP_TENSOR):
+    device-resident HVPs/s, per-kind device time, and the roofline of its
+    dominant kernel (the backward block pass): algorithmic HBM bytes per
+    launch over its event-timed duration, and its tensor-pipe FLOPs. Also
+    returns what the parity check needs: the per-sample overlaps of the full
+    run and grad / HVP of a run on the first m samples (the oracle's sample)."""
+    import numpy as np
+
+    ts = torch.cuda.Stream(device=dev)
+    G = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
+    V = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
+    with native.Context(w.n, w.n_layers, w.psi1q, w.Uref, device=local, stream=ts.cuda_stream, tensor=True) as tc:
+        for _ in range(3):
+            tc.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ts)
+        for _ in range(steps):
+            tc.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None)
+        e1.record(ts)
+        torch.cuda.synchronize(dev)
+        t_ms = e0.elapsed_time(e1) / steps
+        tinfo = tc.plan_info()
+        prof = tc.profile(G.data_ptr(), V.data_ptr())
+        T_full, Om_full = tc.get("T"), tc.get("Omega")
+    kinds = prof["kind"]
+    by_kind = {}
+    for k in sorted(set(kinds.tolist())):
+        sel = kinds == k
+        by_kind[native.KINDS[k]] = dict(launches=int(sel.sum()), ms=float(prof["ms"][sel].sum()),
+                                        flops=float(prof["flops"][sel].sum()),
+                                        bytes=float(prof["bytes"][sel].sum()))
+    total = float(prof["ms"].sum())
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    bw = by_kind.get("block_bwd", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 1})
+    fw = by_kind.get("block_fwd", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 1})
+
+    def _roof(d):
+        gbs = d["bytes"] / max(d["ms"], 1e-9) / 1e6
+        tfl = d["flops"] / max(d["ms"], 1e-9) / 1e9
+        return {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
+                "ms_per_launch": d["ms"] / max(d["launches"], 1), "share_of_step": d["ms"] / total,
+                "tensor_tflops": tfl, "tensor_frac_of_bf16_sustained": tfl / bf16}
+
+    roof_b = dict(_roof(bw), bound="hbm", kernel="tcb_kernel<backward> (fused 5-qubit block, bf16 slice GEMM "
+                  "+ TF32 environment GEMM on tcgen05)", peak_source=src)
+    all_by = sum(by_kind[k]["bytes"] for k in ("block_fwd", "block_bwd") if k in by_kind)
+    all_ms = sum(by_kind[k]["ms"] for k in ("block_fwd", "block_bwd") if k in by_kind)
+    line = {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152), fused 5-qubit blocks on the tensor cores "
+                        "(HVP_TENSOR): exact-integer bf16 slice GEMMs, TF32 environment GEMM, FP64 reductions",
+            "value": 1000.0 / t_ms, "unit": "HVPs/s", "ms_per_step": t_ms, "blocks": tinfo["passes"],
+            "per_kind": by_kind, "roofline": roof_b, "forward_kernel": _roof(fw),
+            "block_passes_hbm": {"achieved_gbs": all_by / max(all_ms, 1e-9) / 1e6,
+                                 "frac": all_by / max(all_ms, 1e-9) / 1e6 / hbm},
+            "device_mib": tinfo["device_mib"]}
+    # a run on the oracle's sample (the first m samples) for grad / HVP parity
+    sub = native.Context(w.n, w.n_layers, w.psi1q[:m], w.Uref, device=local, stream=ts.cuda_stream, tensor=True)
+    with sub:
+        _, g_sub, h_sub = sub.hvp(w.G, w.V)
+    return line, {"T": T_full, "Omega": Om_full, "grad": g_sub, "hvp": h_sub}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,6 +405,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-circuit measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the two-directions-per-sweep measurement")
     ap.add_argument("--no-configs", action="store_true", help="skip the n=12 precision and n=26 autograd lines")
+    ap.add_argument("--no-tensor", action="store_true", help="skip the fused-block tensor-core schedule line")
     ap.add_argument("--samples", type=int, default=64,
                     help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
@@ -356,6 +423,8 @@ def main():
                     help="only time the unfused complex128 sweep at --samples (for profiler captures)")
     ap.add_argument("--quick", action="store_true",
                     help="only the device-resident timing (for profiler captures)")
+    ap.add_argument("--tensor", action="store_true",
+                    help="with --quick: time the fused-block tensor-core schedule (HVP_TENSOR)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -409,11 +478,16 @@ def main():
                               "value": 1000.0 / f_ms, "unit": "HVPs/s", "quick": True}), flush=True)
         return 0
     multi = args.multi and args.quick
-    autotune = not (args.no_autotune or args.threads or args.variant or args.window or multi)
+    tensor = args.tensor and args.quick
+    autotune = not (args.no_autotune or args.threads or args.variant or args.window or multi or tensor)
     stream = torch.cuda.Stream(device=dev)
-    ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
-                         stream=stream.cuda_stream, threads=args.threads, variant=args.variant,
-                         window=args.window, autotune=autotune, recompute=args.recompute, multi_dir=multi)
+    if tensor:
+        ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, device=local, stream=stream.cuda_stream,
+                             tensor=True)
+    else:
+        ctx = native.Context(w.n, w.n_layers, w.psi1q, w.Uref, precision="c64", device=local,
+                             stream=stream.cuda_stream, threads=args.threads, variant=args.variant,
+                             window=args.window, autotune=autotune, recompute=args.recompute, multi_dir=multi)
     K = w.K
     G_dev = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
     if multi:
@@ -468,7 +542,8 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value * (2 if multi else 1), "unit": "HVPs/s",
                               "ms_per_step": ms, "n_samples": args.samples, "quick": True,
-                              "directions_per_step": 2 if multi else 1, "plan": info, "clocks": clocks}),
+                              "directions_per_step": 2 if multi else 1, "tensor": tensor, "plan": info,
+                              "clocks": clocks}),
                   flush=True)
         ctx.close()
         if dist:
@@ -647,6 +722,13 @@ def main():
             "one_direction_sweeps_default_plan": {"value": 2000.0 / best_ms, "ms_per_call": best_ms,
                                                   "window": binfo["window"]}}
 
+    # ------------- the fused-block tensor-core schedule, same workload
+    tensor_extra = None
+    if not args.no_tensor and rank == 0:
+        m_or = max(1, min(w.n_samples, os.cpu_count() or 1))
+        line["tensor_blocks"], tensor_extra = tensor_line(native, torch, dev, local, w, max(3, min(args.steps, 10)),
+                                                          m_or)
+
     # --------------- n = 12 precision comparison and n = 26 autograd form
     if not args.no_configs and rank == 0:
         line["n12_precision"] = n12_precision_line(native, make_workload, torch, dev, local)
@@ -669,6 +751,14 @@ def main():
             "E_rel": _rel(E_gpu[:m], o["E"]), "DE_rel": _rel(DE_gpu[:m], o["DE"])}
         pv = line["parity_vs_oracle"]
         pv["pass"] = all(pv[k] < pv["tolerance"] for k in ("T_rel", "Omega_rel", "E_rel", "DE_rel"))
+        if tensor_extra is not None:
+            tx = tensor_extra
+            tp = {"samples": m, "tolerance": 1e-5, "T_rel": _rel(tx["T"][:m], o["T"]),
+                  "Omega_rel": _rel(tx["Omega"][:m], o["Omega"]), "grad_rel": _rel(tx["grad"], o["grad"]),
+                  "hvp_rel": _rel(tx["hvp"], o["hvp"])}
+            tp["pass"] = all(tp[k] < tp["tolerance"] for k in ("T_rel", "Omega_rel", "grad_rel", "hvp_rel"))
+            line["tensor_blocks"]["parity_vs_oracle"] = tp
+            pv["pass"] = pv["pass"] and tp["pass"]
     if rank == 0:
         print(json.dumps(line), flush=True)
         if not line.get("parity_vs_oracle", {}).get("pass", True):
