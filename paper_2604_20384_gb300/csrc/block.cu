@@ -160,21 +160,33 @@ __global__ void __launch_bounds__(256) block_prep_kernel(const DevBlock* __restr
 
 // T_s = sum conj(phi_s) psi_s^[K], Omega_s = sum conj(phi_s) dpsi_s^[K]
 // (Eq. overlap-general at the end of the circuit; Eq. Omega as phi^dag dpsi),
-// per (sample, chunk) partial sums in FP64.
+// per (sample, chunk) partial sums: FP32 runs of 8 amplitudes summed in FP64.
 __global__ void __launch_bounds__(256) overlap_partial_kernel(const float4* __restrict__ x,
                                                                const float2* __restrict__ phi, double* partial,
                                                                int n, int chunks) {
     const int s = blockIdx.y, t = threadIdx.x;
     const size_t dim = (size_t)1 << n, per = (dim + chunks - 1) / chunks;
     const size_t lo = per * blockIdx.x, hi = min(dim, lo + per);
+    // FP32 fused multiply-adds over runs of 8 amplitudes, each run's sums
+    // added in FP64 (FP64 arithmetic is a small fraction of the FP32 rate).
     double tr = 0, ti = 0, orr = 0, oi = 0;
-    for (size_t i = lo + t; i < hi; i += 256) {
-        const float4 v = x[(size_t)s * dim + i];
-        const float2 p = phi[(size_t)s * dim + i];
-        tr += (double)p.x * v.x + (double)p.y * v.y;
-        ti += (double)p.x * v.y - (double)p.y * v.x;
-        orr += (double)p.x * v.z + (double)p.y * v.w;
-        oi += (double)p.x * v.w - (double)p.y * v.z;
+    for (size_t i = lo + t; i < hi;) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k, i += 256) {
+            if (i < hi) {
+                const float4 v = __ldcs(&x[(size_t)s * dim + i]);
+                const float2 p = __ldg(&phi[(size_t)s * dim + i]);
+                a0 = fmaf(p.x, v.x, fmaf(p.y, v.y, a0));
+                a1 = fmaf(p.x, v.y, fmaf(-p.y, v.x, a1));
+                a2 = fmaf(p.x, v.z, fmaf(p.y, v.w, a2));
+                a3 = fmaf(p.x, v.w, fmaf(-p.y, v.z, a3));
+            }
+        }
+        tr += (double)a0;
+        ti += (double)a1;
+        orr += (double)a2;
+        oi += (double)a3;
     }
     __shared__ double sh[4][256];
     sh[0][t] = tr; sh[1][t] = ti; sh[2][t] = orr; sh[3][t] = oi;
