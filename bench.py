@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(n=20, n_layers=16, n_samples=64, seed=0)
 METRIC = "HVPs/sec (loss+grad+HVP) at n=20,L=16,N_s=64; fraction of HBM roofline"
+MEASURED_FFMA_TFLOPS = 74.6   # FP32 FFMA throughput measured on a GB300 by a register-only loop
 FP32_LANES_PER_SM, N_SM = 128, 152
 
 
@@ -628,6 +629,9 @@ def main():
                 "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
                 "algorithmic_bytes_per_launch": p_by / p_n,
                 "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
+                # measured beside it: a register-only FFMA loop on every SM of this GPU model
+                "peak_measured": MEASURED_FFMA_TFLOPS, "frac_of_measured": achieved / MEASURED_FFMA_TFLOPS,
+                "peak_measured_note": "register-only FFMA loop, 152 SMs, CUDA events (packed fma.rn.f32x2: 75.5)",
                 "forward_kernel": {"achieved": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9,
                                    "frac": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9 / alu_peak,
                                    "share_of_step": fwd["ms"] / total_ms},
