@@ -32,9 +32,11 @@
 // input, rows 4 b + p for p = re c, im c, re dc, im dc, against the forward
 // states at the block's input, contracted over the tile's columns) is a
 // second GEMM on TF32 high and low parts of both operands in shared memory
-// (three products), issued after the tile's co-states are complete. Its per-tile results are added to per-thread FP32 sums
-// (round to nearest) and flushed into the CTA's FP64 record every 16 tiles,
-// so the truncating accumulation spans one tile.
+// (three products), issued after the tile's co-states are complete. The
+// results of two consecutive tiles accumulate in TMEM, then are added to
+// per-thread FP32 sums (round to nearest) and flushed into the CTA's FP64
+// record every 16 such pairs, so the truncating accumulation spans two
+// tiles (24 MMAs).
 //
 // Pipeline. One CTA per SM; warps 0-7 load, slice and stage tiles and run the
 // epilogue, warp 8 owns TMEM and its first lane issues every MMA. A tile's
@@ -517,14 +519,16 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             const unsigned xs0 = smem_u32(xslots);
             const uint64_t kx = (uint64_t)((2u * kLboX) >> 4), ke = (uint64_t)((2u * kLboE) >> 4);
             // P = D Psi^T of one tile: K = its 32 columns, 4 K-steps of 8;
-            // high x high + high x low + low x high.
-            auto env = [&]() {
+            // high x high + high x low + low x high. The environments of two
+            // consecutive tiles (local 2m and 2m + 1) accumulate in TMEM
+            // before the producers read them.
+            auto env = [&](bool onto) {
                 const unsigned ps = smem_u32(psislots), ds = smem_u32(dbuf);
                 const uint64_t ph = sdesc(ps, kLboE, kSboE), pl = sdesc(ps + kERegion, kLboE, kSboE);
                 const uint64_t dh = sdesc(ds, kLboE, kSboE), dl = sdesc(ds + kERegion, kLboE, kSboE);
 #pragma unroll
                 for (int k = 0; k < TN / 8; ++k) {
-                    mma_ss_tf32(tb + kEnvCol, dh + k * ke, ph + k * ke, id_e, k > 0);
+                    mma_ss_tf32(tb + kEnvCol, dh + k * ke, ph + k * ke, id_e, onto || k > 0);
                     mma_ss_tf32(tb + kEnvCol, dh + k * ke, pl + k * ke, id_e, 1);
                     mma_ss_tf32(tb + kEnvCol, dl + k * ke, ph + k * ke, id_e, 1);
                 }
@@ -534,7 +538,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             auto env_of = [&](long long j) -> bool {
                 if (!wait(B_CREADY, (unsigned)(j & 1)) || !wait(B_PREADY, (unsigned)(j & 1))) return false;
                 tc_fence_after();
-                env();
+                env((j & 1) != 0);   // odd tiles add onto the even tile before them
                 return true;
             };
             bool issued = false, ok = true;
@@ -687,9 +691,9 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
 
         // Producers run one tile ahead: in iteration j they stage X of tile
         // j + 1 (its slot is free once the update MMAs of tile j - 1 are
-        // done), then (backward) read the environment of tile j - 1, which
-        // the tensor pipe ran after the update of tile j, so that the
-        // environment of tile j may follow.
+        // done), then (backward, j - 1 odd) read the environment summed over
+        // tiles j - 2 and j - 1, which the tensor pipe ran after the update
+        // of tile j, so that the environment of tile j may start afresh.
         long long j = 0;
         if ((long long)blockIdx.x < ntiles) {
             for (int q = 0; q < RX; ++q) issue_x(q);
@@ -705,10 +709,13 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 produce_x(j + 1, sg);
             }
             if (BWD) {
+                // every tile waits for the previous tile's environment MMAs
+                // (PREADY then never runs two phases ahead of the MMA warp's
+                // wait); the sums are read after odd tiles (tiles j - 2 and j - 1)
                 if (j >= 1) {
                     if (!wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
                     tc_fence_after();
-                    read_env();
+                    if ((j - 1) & 1) read_env();
                 }
                 tc_fence_before();
                 mbar_arrive(&bars[B_PREADY]);
@@ -718,7 +725,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             if (group_sync_or(1, bad)) { ok = false; break; }
             if (more) issue_x(j + 1 + RX);
         }
-        if (BWD && ok && j > 0) {   // the last tile's environment
+        if (BWD && ok && j > 0) {   // the last tile's environment (with the one before it if that is even)
             if (!wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
             if (group_sync_or(1, bad)) {
                 ok = false;
