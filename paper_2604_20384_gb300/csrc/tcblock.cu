@@ -35,7 +35,7 @@
 // (three products), issued after the tile's co-states are complete. The
 // results of two consecutive tiles accumulate in TMEM, then are added to
 // per-thread FP32 sums (round to nearest) and flushed into the CTA's FP64
-// record every 16 such pairs, so the truncating accumulation spans two
+// record every 64 such pairs, so the truncating accumulation spans two
 // tiles (24 MMAs).
 //
 // Pipeline. One CTA per SM; warps 0-7 load, slice and stage tiles and run the
@@ -65,7 +65,7 @@ constexpr unsigned kAccBuf = 3 * NE;         //   of NE columns each
 constexpr unsigned kEnvCol = kAccCol + kAccBuf;  // backward (one buffer): environment, 128 columns
 constexpr unsigned kSumCol = kEnvCol + 128;      // backward: FP32 running sums of environment columns
                                                  //   16..63 of each producer thread's 64 (96 columns)
-constexpr int kFlushTiles = 16;              // FP32 tiles summed before an FP64 flush
+constexpr int kFlushTiles = 64;              // environment reads summed in FP32 before an FP64 flush
 constexpr unsigned kWaitLimit = 1u << 22;    // mbarrier polls before a wait gives up
 constexpr unsigned kSettleLimit = 1u << 16;  // polls for an outstanding copy on the way out
 
@@ -324,6 +324,26 @@ __device__ __forceinline__ void slice3_pair(float re, float im, uint32_t& p0, ui
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p0) : "f"(i0), "f"(r0));
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p1) : "f"(i1), "f"(r1));
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p2) : "f"(i2), "f"(r2));
+}
+
+// Rows 4 b + p (p = the four components, four columns per 16-byte row) of a
+// TF32 operand of the environment GEMM: high parts at dst + base, low parts
+// one region further. One copy of this code serves both operands.
+__device__ __noinline__ void put_tf32_rows(unsigned char* dst, unsigned base, float4 v0, float4 v1, float4 v2,
+                                           float4 v3) {
+    const float4 v[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        float h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float x = p == 0 ? v[i].x : p == 1 ? v[i].y : p == 2 ? v[i].z : v[i].w;
+            h[i] = tf32_rna(x);
+            l[i] = tf32_rna(x - h[i]);
+        }
+        *reinterpret_cast<float4*>(dst + base + 16 * p) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(dst + kERegion + base + 16 * p) = make_float4(l[0], l[1], l[2], l[3]);
+    }
 }
 
 template <bool BWD>
@@ -670,7 +690,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 since_flush = 0;
             }
         };
-        auto read_env = [&]() {
+        auto read_env = [&](bool final) {
             if constexpr (BWD) {
                 float e[16], t[16];
                 tmem_ld16(envc, e);
@@ -685,7 +705,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                     tmem_st16(sumc + 16 * h, t);
                 }
                 tmem_wait_st();
-                if (++since_flush == kFlushTiles) flush();
+                if (++since_flush == kFlushTiles || final) flush();
             }
         };
 
@@ -694,15 +714,19 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         // done), then (backward, j - 1 odd) read the environment summed over
         // tiles j - 2 and j - 1, which the tensor pipe ran after the update
         // of tile j, so that the environment of tile j may start afresh.
-        long long j = 0;
-        if ((long long)blockIdx.x < ntiles) {
+        // (The last environment is read in one more iteration, j == count,
+        // so that the read and its flush exist once in the code.)
+        const long long count = (long long)blockIdx.x < ntiles ? (ntiles - blockIdx.x + g - 1) / g : 0;
+        if (count > 0) {
             for (int q = 0; q < RX; ++q) issue_x(q);
             produce_x(0, 0);
         }
         if (group_sync_or(1, bad)) ok = false;
         else issue_x(RX);
-        for (long long tile = blockIdx.x; ok && tile < ntiles; tile += g, ++j) {
-            const bool more = tile + g < ntiles;
+        for (long long j = 0; ok && j <= count; ++j) {
+            const bool last = j == count;
+            if (last && !(BWD && count > 0)) break;
+            const bool more = j + 1 < count;
             if (more) {
                 const int sg = (int)((j + 1) & 1);
                 if (j >= 1 && !wait(B_XDONE0 + sg, (unsigned)(((j - 1) >> 1) & 1))) bad = true;
@@ -711,30 +735,27 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             if (BWD) {
                 // every tile waits for the previous tile's environment MMAs
                 // (PREADY then never runs two phases ahead of the MMA warp's
-                // wait); the sums are read after odd tiles (tiles j - 2 and j - 1)
+                // wait); the sums are read after odd tiles (tiles j - 2 and
+                // j - 1) and after the last
                 if (j >= 1) {
                     if (!wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
                     tc_fence_after();
-                    if ((j - 1) & 1) read_env();
+                    if (((j - 1) & 1) || last) read_env(last);
                 }
-                tc_fence_before();
-                mbar_arrive(&bars[B_PREADY]);
+                if (!last) {
+                    tc_fence_before();
+                    mbar_arrive(&bars[B_PREADY]);
+                }
             }
             // all leave together if any wait gave up; else every producer has
             // read the ring slots taken above: refill them
             if (group_sync_or(1, bad)) { ok = false; break; }
             if (more) issue_x(j + 1 + RX);
         }
-        if (BWD && ok && j > 0) {   // the last tile's environment (with the one before it if that is even)
-            if (!wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
-            if (group_sync_or(1, bad)) {
-                ok = false;
-            } else {
-                tc_fence_after();
-                read_env();
-            }
+        if (BWD && ok && count == 0) {   // no tiles: this CTA's record is zero
+            double* dst = a.rec + (size_t)blockIdx.x * 16384 + (size_t)row * 128 + 64 * (warp >> 2);
+            for (int i = 0; i < 64; ++i) dst[i] = 0.0;
         }
-        if (ok && BWD && (since_flush > 0 || !flushed)) flush();
         settle(x_taken, x_issued, 0, RX);
     } else {
         // ------------------------------------------------------------ epilogue
@@ -801,20 +822,8 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             if constexpr (BWD) {
                 float4 v[4];
                 take(j, RX + (int)(j % RP), (int)(j / RP), true, v);
-                const unsigned base = (unsigned)qd * kLboE + ((unsigned)lane >> 1) * kSboE + ((unsigned)lane & 1u) * 64u;
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float h[4], l[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float x = p == 0 ? v[i].x : p == 1 ? v[i].y : p == 2 ? v[i].z : v[i].w;
-                        h[i] = tf32_rna(x);
-                        l[i] = tf32_rna(x - h[i]);
-                    }
-                    *reinterpret_cast<float4*>(psislots + base + 16 * p) = make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4*>(psislots + kERegion + base + 16 * p) =
-                        make_float4(l[0], l[1], l[2], l[3]);
-                }
+                put_tf32_rows(psislots, (unsigned)qd * kLboE + ((unsigned)lane >> 1) * kSboE + ((unsigned)lane & 1u) * 64u,
+                              v[0], v[1], v[2], v[3]);
                 fence_async_smem();
             }
         };
@@ -866,18 +875,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
 #pragma unroll
                 for (int k = 0; k < 4; ++k) o[k] = out(ub, (unsigned)(4 * e + k));
                 produce_psi(j);
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float h[4], l[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float x = p == 0 ? o[i].x : p == 1 ? o[i].y : p == 2 ? o[i].z : o[i].w;
-                        h[i] = tf32_rna(x);
-                        l[i] = tf32_rna(x - h[i]);
-                    }
-                    *reinterpret_cast<float4*>(dbuf + base + 16 * p) = make_float4(h[0], h[1], h[2], h[3]);
-                    *reinterpret_cast<float4*>(dbuf + kERegion + base + 16 * p) = make_float4(l[0], l[1], l[2], l[3]);
-                }
+                put_tf32_rows(dbuf, base, o[0], o[1], o[2], o[3]);
                 fence_async_smem();
                 mbar_arrive(&bars[B_CREADY]);
             }
