@@ -1,9 +1,11 @@
 """Benchmark: HVPs/s (loss + gradient + HVP per call) of the brickwall workload
-n = 20, L = 16 (K = 152 gates), N_s = 64 Haar product states, complex64 window
-passes with FP64 accumulation, on synthetic seeded inputs.
+n = 20, L = 16 (K = 152 gates), N_s = 64 Haar product states, complex64 states
+with FP64 accumulation, on synthetic seeded inputs.
 
-One step = one full evaluation (every window pass plus the FP64 post-
-processing) of the whole workload. `value` is measured with the inputs
+One step = one full evaluation of the whole workload (every pass plus the FP64
+post-processing) in the schedule the library's autotuner picks at set-up: the
+fused 5-qubit blocks on the tensor cores or the SIMT window passes; the other
+schedule is timed on a line of its own. `value` is measured with the inputs
 resident in HBM (stream-ordered device-pointer call replaying the captured
 CUDA graph, CUDA events on the library's stream); `e2e` times the host-memory
 C ABI call (G, V uploaded and every result downloaded each step).
@@ -34,8 +36,17 @@ MEASURED_FFMA_TFLOPS = 74.6   # FP32 FFMA throughput measured on a GB300 by a re
 FP32_LANES_PER_SM, N_SM = 128, 152
 
 
-KERNEL_SOURCES = ["paper_2604_20384_gb300/csrc/tiled.cu", "paper_2604_20384_gb300/csrc/tiled_common.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_n20_L16_Ns64.json")
+# Per schedule: the sources of its dominant (backward) kernel, whose committed
+# DRAM traffic record counts only while they are unchanged, the record, and
+# the plan fields a record must match.
+KERNEL_SOURCES = {
+    "window": ["paper_2604_20384_gb300/csrc/tiled.cu", "paper_2604_20384_gb300/csrc/tiled_common.cuh"],
+    "tensor": ["paper_2604_20384_gb300/csrc/tcblock.cu", "paper_2604_20384_gb300/csrc/internal.h"],
+}
+TRAFFIC_FILES = {"window": os.path.join(ROOT, "profiles", "traffic_n20_L16_Ns64.json"),
+                 "tensor": os.path.join(ROOT, "profiles", "traffic_tcb_n20_L16_Ns64.json")}
+PLAN_KEYS = {"window": ("window", "threads", "variant", "passes", "checkpoint_stride"),
+             "tensor": ("window", "passes", "variant")}
 
 
 def strip_comments(src: str) -> str:
@@ -46,29 +57,28 @@ def strip_comments(src: str) -> str:
     return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
 
 
-def kernel_source_hash() -> str:
-    """Hash of the code (comments stripped) of the window-pass kernel sources."""
+def kernel_source_hash(schedule: str = "window") -> str:
+    """Hash of the code (comments stripped) of a schedule's kernel sources."""
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[schedule]:
         with open(os.path.join(ROOT, rel)) as f:
             h.update(strip_comments(f.read()).encode())
     return h.hexdigest()
 
 
-def recorded_traffic(info):
+def recorded_traffic(info, schedule: str = "window"):
     """DRAM bytes per backward-kernel launch from the committed ncu capture, if
-    it was taken on the current kernel sources and the same plan (window,
-    threads, arithmetic), else None."""
+    it was taken on the current kernel sources and the same plan, else None."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(TRAFFIC_FILES[schedule]) as f:
             doc = json.load(f)
     except (OSError, ValueError):
         return None
-    if doc.get("source_sha256") != kernel_source_hash():
+    if doc.get("source_sha256") != kernel_source_hash(schedule):
         return None
     for rec in doc.get("records", []):
         plan = rec.get("plan", {})
-        if all(plan.get(k) == info[k] for k in ("window", "threads", "variant", "passes", "checkpoint_stride")):
+        if all(plan.get(k) == info[k] for k in PLAN_KEYS[schedule]):
             return rec.get("bwd_kernel_bytes_per_launch")
     return None
 
@@ -329,70 +339,174 @@ def n26_autograd_line(make_workload, torch, dev, local) -> dict:
             "device_mib": info["device_mib"]}
 
 
-def tensor_line(native, torch, dev, local, w, steps: int, m: int):
-    """The same workload on the fused-block tensor-core schedule (HVP_TENSOR):
-    device-resident HVPs/s, per-kind device time, and the roofline of its
-    dominant kernel (the backward block pass): algorithmic HBM bytes per
-    launch over its event-timed duration, and its tensor-pipe FLOPs. Also
-    returns what the parity check needs: the per-sample overlaps of the full
-    run and grad / HVP of a run on the first m samples (the oracle's sample)."""
+def kinds_summary(native, prof) -> dict:
+    """Per launch kind of one profiled call: launches, device ms, flops and
+    algorithmic bytes."""
+    kinds = prof["kind"]
+    out = {}
+    for k in sorted(set(kinds.tolist())):
+        sel = kinds == k
+        out[native.KINDS[k]] = dict(launches=int(sel.sum()), ms=float(prof["ms"][sel].sum()),
+                                    flops=float(prof["flops"][sel].sum()), bytes=float(prof["bytes"][sel].sum()))
+    return out
+
+
+def window_roofline(by_kind, info, total_ms, peaks, src):
+    """Roofline of the window-pass schedule's dominant kernel, the backward
+    window-pass kernel (backward passes and, when forward states are
+    recomputed, the turnaround pass). Its arithmetic is FP32 SIMT, so the
+    bound is the FP32 lane rate at the maximum SM clock; with the forward cache
+    it also streams 16 B per amplitude per gate from HBM (the HBM fraction is
+    reported beside it). Also returns the step's HBM fraction: every window
+    pass's algorithmic bytes over their time."""
+    cached = info["checkpoint_stride"] == 0
+    bwd_kinds = [k for k in ("pass_bwd", "pass_turnaround") if k in by_kind]
+    p_ms = sum(by_kind[k]["ms"] for k in bwd_kinds)
+    p_fl = sum(by_kind[k]["flops"] for k in bwd_kinds)
+    p_by = sum(by_kind[k]["bytes"] for k in bwd_kinds)
+    p_n = sum(by_kind[k]["launches"] for k in bwd_kinds)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s
+    achieved = (p_fl / p_n) / (p_ms / p_n / 1e3) / 1e12
+    fwd = by_kind.get("pass_fwd", {"ms": 0.0, "flops": 0.0, "launches": 0})
+    all_ms = sum(by_kind[k]["ms"] for k in by_kind if k.startswith("pass_"))
+    all_fl = sum(by_kind[k]["flops"] for k in by_kind if k.startswith("pass_"))
+    all_by = sum(by_kind[k]["bytes"] for k in by_kind if k.startswith("pass_"))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": recorded_traffic(info, "window"),
+                "kernel": (f"tiled_bwdc_kernel<tangent, {info['threads']} threads> (backward window passes "
+                           f"reading the forward cache, window {info['window']})" if cached else
+                           f"tiled_bwd_kernel<tangent, {'packed' if info['variant'] == 2 else 'scalar'}, "
+                           f"{info['threads']} threads> (backward and turnaround window passes, "
+                           f"window {info['window']})"),
+                "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
+                "algorithmic_bytes_per_launch": p_by / p_n,
+                "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
+                # measured beside it: a register-only FFMA loop on every SM of this GPU model
+                "peak_measured": MEASURED_FFMA_TFLOPS, "frac_of_measured": achieved / MEASURED_FFMA_TFLOPS,
+                "peak_measured_note": "register-only FFMA loop, 152 SMs, CUDA events (packed fma.rn.f32x2: 75.5)",
+                "forward_kernel": {"achieved": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9,
+                                   "frac": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9 / alu_peak,
+                                   "share_of_step": fwd["ms"] / total_ms},
+                "all_window_passes": {"achieved": all_fl / (all_ms / 1e3) / 1e12,
+                                      "frac": all_fl / (all_ms / 1e3) / 1e12 / alu_peak},
+                "hbm": {"achieved_gbs": p_by / (p_ms / 1e3) / 1e9, "peak_gbs": hbm_peak,
+                        "frac": (p_by / (p_ms / 1e3) / 1e9) / hbm_peak, "peak_source": src}}
+    gbs = all_by / (all_ms / 1e3) / 1e9
+    # every window pass of the step: the schedule's algorithmic bytes (state I/O and, with the
+    # forward cache, 16 B per amplitude per gate written and read back) over their time
+    hbm = {"frac": gbs / hbm_peak, "achieved_gbs": gbs, "peak_gbs": hbm_peak, "peak_source": src,
+           "bytes_per_step": all_by, "over": "window passes"}
+    return roofline, hbm
+
+
+def tensor_roofline(by_kind, info, total_ms, peaks, src):
+    """Roofline of the fused-block tensor-core schedule's dominant kernel, the
+    backward block pass: algorithmic HBM bytes per launch (co-states read and
+    written, forward states read: 48 B per amplitude, 32 B in the last pass)
+    over its event-timed duration against the measured copy bandwidth, with
+    its tensor-pipe rate beside it. Also returns the step's HBM fraction: every
+    block pass's algorithmic bytes over their time."""
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    bw = by_kind.get("block_bwd", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 1})
+    fw = by_kind.get("block_fwd", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 1})
+
+    def _rate(d):
+        n = max(d["launches"], 1)
+        per_ms = max(d["ms"], 1e-9) / n
+        gbs = d["bytes"] / n / per_ms / 1e6
+        tfl = d["flops"] / n / per_ms / 1e9
+        return {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "algorithmic_bytes_per_launch": d["bytes"] / n, "ms_per_launch": per_ms, "launches_per_step": n,
+                "share_of_step": d["ms"] / total_ms, "tensor_pipe": {
+                    "achieved_tflops": tfl, "peak_tflops": bf16, "frac": tfl / bf16,
+                    "note": "bf16 slice products and TF32 environment products issued, against the measured "
+                            "sustained bf16 cuBLAS rate"}}
+
+    roofline = dict(_rate(bw), bound="hbm", traffic=recorded_traffic(info, "tensor"), peak_source=src,
+                    kernel="tcb_kernel<backward> (fused 5-qubit block: exact-integer bf16 slice GEMM and TF32 "
+                           "environment GEMM on tcgen05, TMA tile loads)")
+    roofline["forward_kernel"] = _rate(fw)
+    all_by = bw["bytes"] + fw["bytes"]
+    all_ms = bw["ms"] + fw["ms"]
+    gbs = all_by / max(all_ms, 1e-9) / 1e6
+    hbm = {"frac": gbs / hbm_peak, "achieved_gbs": gbs, "peak_gbs": hbm_peak, "peak_source": src,
+           "bytes_per_step": all_by, "over": "block passes"}
+    return roofline, hbm
+
+
+def parity_outputs(native, ctx, w, m: int, local: int, stream, tensor: bool) -> dict:
+    """What the parity check compares with the oracle's run on the first m
+    samples, read after a full (tangent) call of ctx: the per-sample overlaps
+    T and Omega and, for the window-pass schedule, the per-sample
+    environments E and DE; the tensor schedule keeps no per-sample
+    environments, so a context on the first m samples gives the gradient and
+    HVP instead (sums over those samples)."""
+    d = {"T": ctx.get("T"), "Omega": ctx.get("Omega")}
+    if tensor:
+        with native.Context(w.n, w.n_layers, w.psi1q[:m], w.Uref, device=local, stream=stream, tensor=True) as sub:
+            _, d["grad"], d["hvp"] = sub.hvp(w.G, w.V)
+    else:
+        d["E"], d["DE"] = ctx.get("env")
+    return d
+
+
+def parity_check(d: dict, o: dict, m: int, tol: float = 1e-5) -> dict:
+    """Relative errors of parity_outputs against the oracle's outputs."""
+    import numpy as np
+
+    def _rel(a, b):
+        return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+    per_sample = ("T", "Omega", "E", "DE")
+    res = {"samples": m, "tolerance": tol}
+    for k in ("T", "Omega", "E", "DE", "grad", "hvp"):
+        if k in d:
+            res[k + "_rel"] = _rel(d[k][:m] if k in per_sample else d[k], o[k])
+    res["pass"] = all(v < tol for k, v in res.items() if k.endswith("_rel"))
+    return res
+
+
+def schedule_line(native, torch, dev, local, w, steps: int, m: int, tensor: bool):
+    """The same workload on the schedule the autotuner did not pick: the
+    fused-block tensor-core schedule (HVP_TENSOR), or the window passes with
+    the forward cache (12-qubit windows, 256 threads, scalar arithmetic).
+    Device-resident HVPs/s, per-kind device time, the roofline of its dominant
+    kernel, and what its parity check needs."""
     import numpy as np
 
     ts = torch.cuda.Stream(device=dev)
     G = torch.from_numpy(w.G.view(np.float64).reshape(-1).copy()).to(dev)
     V = torch.from_numpy(w.V.view(np.float64).reshape(-1).copy()).to(dev)
-    with native.Context(w.n, w.n_layers, w.psi1q, w.Uref, device=local, stream=ts.cuda_stream, tensor=True) as tc:
+    kw = dict(tensor=True) if tensor else dict(precision="c64", window=12, threads=256, variant=1)
+    with native.Context(w.n, w.n_layers, w.psi1q, w.Uref, device=local, stream=ts.cuda_stream, **kw) as c:
         for _ in range(3):
-            tc.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None)
+            c.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(ts)
         for _ in range(steps):
-            tc.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None)
+            c.hvp_dev(G.data_ptr(), V.data_ptr(), None, None, None)
         e1.record(ts)
         torch.cuda.synchronize(dev)
         t_ms = e0.elapsed_time(e1) / steps
-        tinfo = tc.plan_info()
-        prof = tc.profile(G.data_ptr(), V.data_ptr())
-        T_full, Om_full = tc.get("T"), tc.get("Omega")
-    kinds = prof["kind"]
-    by_kind = {}
-    for k in sorted(set(kinds.tolist())):
-        sel = kinds == k
-        by_kind[native.KINDS[k]] = dict(launches=int(sel.sum()), ms=float(prof["ms"][sel].sum()),
-                                        flops=float(prof["flops"][sel].sum()),
-                                        bytes=float(prof["bytes"][sel].sum()))
+        info = c.plan_info()
+        prof = c.profile(G.data_ptr(), V.data_ptr())
+        c.hvp(w.G, w.V)
+        par = parity_outputs(native, c, w, m, local, ts.cuda_stream, tensor)
+    by_kind = kinds_summary(native, prof)
     total = float(prof["ms"].sum())
     peaks, src = _peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
-    bw = by_kind.get("block_bwd", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 1})
-    fw = by_kind.get("block_fwd", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 1})
-
-    def _roof(d):
-        gbs = d["bytes"] / max(d["ms"], 1e-9) / 1e6
-        tfl = d["flops"] / max(d["ms"], 1e-9) / 1e9
-        return {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
-                "ms_per_launch": d["ms"] / max(d["launches"], 1), "share_of_step": d["ms"] / total,
-                "tensor_tflops": tfl, "tensor_frac_of_bf16_sustained": tfl / bf16}
-
-    roof_b = dict(_roof(bw), bound="hbm", kernel="tcb_kernel<backward> (fused 5-qubit block, bf16 slice GEMM "
-                  "+ TF32 environment GEMM on tcgen05)", peak_source=src)
-    all_by = sum(by_kind[k]["bytes"] for k in ("block_fwd", "block_bwd") if k in by_kind)
-    all_ms = sum(by_kind[k]["ms"] for k in ("block_fwd", "block_bwd") if k in by_kind)
-    line = {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152), fused 5-qubit blocks on the tensor cores "
-                        "(HVP_TENSOR): exact-integer bf16 slice GEMMs, TF32 environment GEMM, FP64 reductions",
-            "value": 1000.0 / t_ms, "unit": "HVPs/s", "ms_per_step": t_ms, "blocks": tinfo["passes"],
-            "per_kind": by_kind, "roofline": roof_b, "forward_kernel": _roof(fw),
-            "block_passes_hbm": {"achieved_gbs": all_by / max(all_ms, 1e-9) / 1e6,
-                                 "frac": all_by / max(all_ms, 1e-9) / 1e6 / hbm},
-            "device_mib": tinfo["device_mib"]}
-    # a run on the oracle's sample (the first m samples) for grad / HVP parity
-    sub = native.Context(w.n, w.n_layers, w.psi1q[:m], w.Uref, device=local, stream=ts.cuda_stream, tensor=True)
-    with sub:
-        _, g_sub, h_sub = sub.hvp(w.G, w.V)
-    return line, {"T": T_full, "Omega": Om_full, "grad": g_sub, "hvp": h_sub}
+    roof, hbm = (tensor_roofline if tensor else window_roofline)(by_kind, info, total, peaks, src)
+    line = {"workload": ("brickwall HVP n=20 L=16 N_s=64 (K=152), " +
+                         ("fused 5-qubit blocks on the tensor cores (HVP_TENSOR): exact-integer bf16 slice GEMMs, "
+                          "TF32 environment GEMM, FP64 reductions" if tensor else
+                          "complex64 window passes with the forward cache, FP64 accumulation")),
+            "value": 1000.0 / t_ms, "unit": "HVPs/s", "ms_per_step": t_ms, "plan": info,
+            "per_kind": by_kind, "roofline": roof, "hbm_roofline": hbm}
+    return line, par
 
 
 def main():
@@ -406,7 +520,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-circuit measurement")
     ap.add_argument("--no-multi", action="store_true", help="skip the two-directions-per-sweep measurement")
     ap.add_argument("--no-configs", action="store_true", help="skip the n=12 precision and n=26 autograd lines")
-    ap.add_argument("--no-tensor", action="store_true", help="skip the fused-block tensor-core schedule line")
+    ap.add_argument("--no-other", "--no-tensor", dest="no_other", action="store_true",
+                    help="skip the line of the schedule the autotuner did not pick")
     ap.add_argument("--samples", type=int, default=64,
                     help="N_s of the workload (64 is the benchmark; smaller only for profiler captures)")
     ap.add_argument("--threads", type=int, default=0, help="window-pass kernel threads (0 = library default)")
@@ -571,10 +686,12 @@ def main():
     e2e = {"value": world * 1000.0 / e2e_ms, "unit": "HVPs/s", "h2d_bytes_per_step": 2 * 32 * K * 8,
            "d2h_bytes_per_step": res_doubles * 8 + 4, "ms_per_step": e2e_ms}
 
-    # ------------------------------------------- per-launch roofline (events)
+    # hvp_plan_info marks the fused-block tensor-core schedule with arithmetic variant 0
+    tensor_plan = info["variant"] == 0
+    schedule = "tensor" if tensor_plan else "window"
     # per-sample outputs of the last (host-array) call, for the parity check
-    T_gpu, Om_gpu = ctx.get("T"), ctx.get("Omega")
-    E_gpu, DE_gpu = ctx.get("env")
+    m_or = max(1, min(w.n_samples, os.cpu_count() or 1))
+    par = parity_outputs(native, ctx, w, m_or, local, stream.cuda_stream, tensor_plan) if rank == 0 else None
 
     # ------------------------------- loss and gradient only (no tangent sweep; after the
     # per-sample outputs of the last HVP call were read)
@@ -591,81 +708,40 @@ def main():
     loss_grad_line = {"workload": "n=20 L=16 N_s=64, loss and gradient only (Alg. 1 without tangents)",
                       "value": world * 1000.0 / lg_ms, "unit": "evaluations/s", "ms_per_step": lg_ms}
 
+    # ------------------------------------------- per-launch roofline (events)
     prof = ctx.profile(G_dev.data_ptr(), V_dev.data_ptr())
-    kinds = prof["kind"]
-    by_kind = {}
-    for k in sorted(set(kinds.tolist())):
-        sel = kinds == k
-        by_kind[native.KINDS[k]] = dict(launches=int(sel.sum()), ms=float(prof["ms"][sel].sum()),
-                                        flops=float(prof["flops"][sel].sum()),
-                                        bytes=float(prof["bytes"][sel].sum()))
+    by_kind = kinds_summary(native, prof)
     total_ms = float(prof["ms"].sum())
-    # Dominant kernel: the backward window-pass kernel (backward passes and,
-    # when forward states are recomputed, the turnaround pass). Its arithmetic
-    # is FP32 SIMT, so the roofline is the FP32 lane rate at the maximum SM
-    # clock; with the forward cache it also streams 16 B per amplitude per gate
-    # from HBM (the HBM fraction is reported beside it).
-    cached = info["checkpoint_stride"] == 0
-    bwd_kinds = [k for k in ("pass_bwd", "pass_turnaround") if k in by_kind]
-    p_ms = sum(by_kind[k]["ms"] for k in bwd_kinds)
-    p_fl = sum(by_kind[k]["flops"] for k in bwd_kinds)
-    p_by = sum(by_kind[k]["bytes"] for k in bwd_kinds)
-    p_n = sum(by_kind[k]["launches"] for k in bwd_kinds)
     peaks, src = _peaks()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12       # TFLOP/s
-    achieved = (p_fl / p_n) / (p_ms / p_n / 1e3) / 1e12
-    fwd = by_kind.get("pass_fwd", {"ms": 0.0, "flops": 0.0, "launches": 0})
-    all_ms = sum(by_kind[k]["ms"] for k in by_kind if k.startswith("pass_"))
-    all_fl = sum(by_kind[k]["flops"] for k in by_kind if k.startswith("pass_"))
-    all_by = sum(by_kind[k]["bytes"] for k in by_kind if k.startswith("pass_"))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": recorded_traffic(info),
-                "kernel": (f"tiled_bwdc_kernel<tangent, {info['threads']} threads> (backward window passes "
-                           f"reading the forward cache, window {info['window']})" if cached else
-                           f"tiled_bwd_kernel<tangent, {'packed' if info['variant'] == 2 else 'scalar'}, "
-                           f"{info['threads']} threads> (backward and turnaround window passes, "
-                           f"window {info['window']})"),
-                "launches_per_step": p_n, "share_of_step": p_ms / total_ms,
-                "algorithmic_bytes_per_launch": p_by / p_n,
-                "peak_note": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (unit counts and max clock)",
-                # measured beside it: a register-only FFMA loop on every SM of this GPU model
-                "peak_measured": MEASURED_FFMA_TFLOPS, "frac_of_measured": achieved / MEASURED_FFMA_TFLOPS,
-                "peak_measured_note": "register-only FFMA loop, 152 SMs, CUDA events (packed fma.rn.f32x2: 75.5)",
-                "forward_kernel": {"achieved": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9,
-                                   "frac": fwd["flops"] / max(fwd["ms"], 1e-9) / 1e9 / alu_peak,
-                                   "share_of_step": fwd["ms"] / total_ms},
-                "all_window_passes": {"achieved": all_fl / (all_ms / 1e3) / 1e12,
-                                      "frac": all_fl / (all_ms / 1e3) / 1e12 / alu_peak},
-                "hbm": {"achieved_gbs": p_by / (p_ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs"),
-                        "frac": (p_by / (p_ms / 1e3) / 1e9) / peaks.get("hbm_gbs", 6800.0),
-                        "peak_source": src},
-                # every window pass of the step: the schedule's algorithmic bytes (state I/O and, with
-                # the forward cache, 16 B per amplitude per gate written and read back) over their time
-                "step_hbm": {"achieved_gbs": all_by / (all_ms / 1e3) / 1e9,
-                             "frac": (all_by / (all_ms / 1e3) / 1e9) / peaks.get("hbm_gbs", 6800.0),
-                             "bytes_per_step": all_by}}
+    roofline, hbm_roofline = (tensor_roofline if tensor_plan else window_roofline)(by_kind, info, total_ms, peaks,
+                                                                                   src)
+    cached = info["checkpoint_stride"] == 0
+    if tensor_plan:
+        workload = ("brickwall HVP n=20 L=16 N_s=64 (K=152), fused 5-qubit blocks on the tensor cores "
+                    "(exact-integer bf16 slice GEMMs, TF32 environment GEMM), complex64 states, FP64 accumulation")
+        sched_text = ("fused 5-qubit blocks (App. D): the forward states at every block boundary kept, "
+                      "block operators applied on tcgen05 tensor cores, per-gate environments by FP64 cuts")
+    else:
+        workload = "brickwall HVP n=20 L=16 N_s=64 (K=152), complex64 window passes, FP64 accumulation"
+        sched_text = ("forward states of every gate cached (Alg. 1), read back by bulk copies"
+                      if cached else "forward states recomputed inside each window pass")
 
     line = {"metric": METRIC, "value": value, "unit": "HVPs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64",
             "data": "synthetic (seeded Haar brickwall, Haar product states)",
-            "config": {"workload": "brickwall HVP n=20 L=16 N_s=64 (K=152), complex64 window passes, "
-                                   "FP64 accumulation", "n": 20, "L": 16, "N_s": 64, "K": K,
+            "config": {"workload": workload, "n": 20, "L": 16, "N_s": 64, "K": K,
+                       "schedule_kind": schedule,
                        "window": info["window"], "passes": info["passes"], "threads": info["threads"],
                        "variant": info["variant"], "autotuned": autotune,
                        "checkpoint_stride": info["checkpoint_stride"], "tiles_per_cta": info["tiles_per_cta"],
-                       "schedule": ("forward states of every gate cached (Alg. 1), read back by bulk copies"
-                                    if cached else "forward states recomputed inside each window pass"),
-                       "device_mib": info["device_mib"],
+                       "schedule": sched_text, "device_mib": info["device_mib"],
                        "l2": "inputs larger than L2 (512 MiB per state set, 129 MB L2)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
-            # the metric's HBM-roofline fraction: the whole step's algorithmic bytes over the window passes'
-            # time against the measured copy bandwidth
-            "hbm_roofline": {"frac": roofline["step_hbm"]["frac"], "achieved_gbs": roofline["step_hbm"]["achieved_gbs"],
-                             "peak_gbs": peaks.get("hbm_gbs"), "peak_source": src,
-                             "bytes_per_step": roofline["step_hbm"]["bytes_per_step"]},
+            # the metric's HBM-roofline fraction: the step's algorithmic bytes over the time of the
+            # passes that move them, against the measured copy bandwidth
+            "hbm_roofline": hbm_roofline,
             "e2e": e2e, "gpu_launches": info["launches_per_hvp"] * args.steps,
             "clocks": clocks, "per_kind": by_kind, "loss_grad_only": loss_grad_line}
 
@@ -726,12 +802,12 @@ def main():
             "one_direction_sweeps_default_plan": {"value": 2000.0 / best_ms, "ms_per_call": best_ms,
                                                   "window": binfo["window"]}}
 
-    # ------------- the fused-block tensor-core schedule, same workload
-    tensor_extra = None
-    if not args.no_tensor and rank == 0:
-        m_or = max(1, min(w.n_samples, os.cpu_count() or 1))
-        line["tensor_blocks"], tensor_extra = tensor_line(native, torch, dev, local, w, max(3, min(args.steps, 10)),
-                                                          m_or)
+    # -------------- the schedule the autotuner did not pick, same workload
+    other = None
+    if not args.no_other and rank == 0:
+        key = "window_passes" if tensor_plan else "tensor_blocks"
+        line[key], other = schedule_line(native, torch, dev, local, w, max(3, min(args.steps, 10)), m_or,
+                                         not tensor_plan)
 
     # --------------- n = 12 precision comparison and n = 26 autograd form
     if not args.no_configs and rank == 0:
@@ -741,27 +817,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
         line["cpu_baseline"] = {k: v for k, v in cb.items() if k not in ("seconds_per_step", "steps", "oracle_out")}
-        # Parity of the timed configuration against the same oracle run, on the
-        # samples it covered: per-sample overlaps and environments (the
-        # sample-summed outputs are linear in them).
+        # Parity of the timed configuration (and of the other schedule's line)
+        # against the same oracle run, on the samples it covered.
         o, m = cb["oracle_out"], cb["cores"]
-
-        def _rel(a, b):
-            return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
-
-        line["parity_vs_oracle"] = {
-            "samples": m, "tolerance": 1e-5,
-            "T_rel": _rel(T_gpu[:m], o["T"]), "Omega_rel": _rel(Om_gpu[:m], o["Omega"]),
-            "E_rel": _rel(E_gpu[:m], o["E"]), "DE_rel": _rel(DE_gpu[:m], o["DE"])}
-        pv = line["parity_vs_oracle"]
-        pv["pass"] = all(pv[k] < pv["tolerance"] for k in ("T_rel", "Omega_rel", "E_rel", "DE_rel"))
-        if tensor_extra is not None:
-            tx = tensor_extra
-            tp = {"samples": m, "tolerance": 1e-5, "T_rel": _rel(tx["T"][:m], o["T"]),
-                  "Omega_rel": _rel(tx["Omega"][:m], o["Omega"]), "grad_rel": _rel(tx["grad"], o["grad"]),
-                  "hvp_rel": _rel(tx["hvp"], o["hvp"])}
-            tp["pass"] = all(tp[k] < tp["tolerance"] for k in ("T_rel", "Omega_rel", "grad_rel", "hvp_rel"))
-            line["tensor_blocks"]["parity_vs_oracle"] = tp
+        pv = line["parity_vs_oracle"] = parity_check(par, o, m)
+        if other is not None:
+            tp = line[key]["parity_vs_oracle"] = parity_check(other, o, m)
             pv["pass"] = pv["pass"] and tp["pass"]
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -267,7 +267,9 @@ int hvp_get(hvp_ctx *ctx, int what, double *out);
  *   info[8] = threads per CTA, info[9] = arithmetic variant.
  * With HVP_TENSOR: info[1] = number of fused blocks, info[2] = 5 (block
  * qubits), info[3] = 0, info[6] = 0, info[7] = CTAs of the backward block
- * passes, info[8] = 256, info[9] = 0 (TF32 tensor-core arithmetic). */
+ * passes, info[8] = 256, info[9] = 0 (the tensor-core arithmetic: exact-
+ * integer bf16 slice products and TF32 environment products; the window-
+ * pass variants are 1 to 3). */
 int hvp_plan_info(const hvp_ctx *ctx, long long info[10]);
 
 /* Fused-block plan of the HVP_TENSOR schedule without a context or GPU (for

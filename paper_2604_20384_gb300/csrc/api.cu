@@ -118,6 +118,7 @@ struct hvp_ctx {
     Mats64* d_mats64 = nullptr;     // FP64 G, G^-1, V, Y per gate (block post-processing)
     uint32_t* d_ops = nullptr;      // per block: the operator record (integer slices and row scales)
     std::vector<void*> tstate;      // forward states at the output of block j (float4 per amplitude)
+    void* d_psi0 = nullptr;         // the product input states (psi, 0), float4 per amplitude
     double* d_rec = nullptr;        // per block and CTA: FP64 environment records (128 x 128)
     double* d_psum = nullptr;       // per block: records summed over CTAs
     double2* d_Ew = nullptr;        // per gate: sum_s conj(T_s) E_s
@@ -474,18 +475,17 @@ int enqueue_tensor(hvp_ctx* c, bool tan) {
     for (int j = 0; j < nb; ++j) {
         TcbArgs a{};
         a.ops = c->d_ops + (size_t)j * kOpWords;
-        a.xin = j ? reinterpret_cast<const float4*>(c->tstate[j - 1]) : nullptr;
+        a.xin = reinterpret_cast<const float4*>(j ? c->tstate[j - 1] : c->d_psi0);
         a.xout = reinterpret_cast<float4*>(c->tstate[j]);
-        a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
         a.status = c->d_status;
         a.ncols = ncols;
         a.n = n;
         a.a = c->blocks[j].a;
-        a.mode = (j == 0 ? TCB_GEN : 0) | (tan ? 0 : TCB_NO_TANGENT);
+        a.mode = tan ? 0 : TCB_NO_TANGENT;
         a.wait_limit = c->tc_wait_limit;
         a.barrier_extra = c->tc_barrier_extra;
         CUDA_TRY(c, launch_tcb(a, false, c->tc_ctas_fwd, c->stream));
-        if ((rc = prof_mark(c, HVP_K_BLOCK_FWD, amps * fl_fwd, amps * (j ? 32.0 : 16.0)))) return rc;
+        if ((rc = prof_mark(c, HVP_K_BLOCK_FWD, amps * fl_fwd, amps * 32.0))) return rc;
         ++L;
     }
     CUDA_TRY(c, launch_overlaps(reinterpret_cast<const float4*>(c->tstate[nb - 1]),
@@ -493,27 +493,27 @@ int enqueue_tensor(hvp_ctx* c, bool tan) {
                                 c->stream));
     if ((rc = prof_mark(c, HVP_K_POST, 0.0, amps * 24.0))) return rc;
     L += 2;
+    // the co-states entering the backward sweep, weighted by the overlaps
+    CUDA_TRY(c, launch_weighted_phi(reinterpret_cast<const float2*>(c->d_phi), frob ? nullptr : T, frob ? nullptr : Om,
+                                    reinterpret_cast<float4*>(c->d_co), n, ns, c->stream));
+    if ((rc = prof_mark(c, HVP_K_POST, 0.0, amps * 24.0))) return rc;
+    ++L;
     for (int j = nb - 1; j >= 0; --j) {
         TcbArgs a{};
         a.ops = c->d_ops + (size_t)j * kOpWords;
         a.xin = reinterpret_cast<const float4*>(c->d_co);
         a.xout = reinterpret_cast<float4*>(c->d_co);
-        a.psi = j ? reinterpret_cast<const float4*>(c->tstate[j - 1]) : nullptr;
-        a.phi = reinterpret_cast<const float2*>(c->d_phi);
-        a.w1 = frob ? nullptr : T;
-        a.w2 = frob ? nullptr : Om;
-        a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
+        a.psi = reinterpret_cast<const float4*>(j ? c->tstate[j - 1] : c->d_psi0);
         a.rec = c->d_rec + (size_t)j * c->tc_ctas_bwd * 16384;
         a.status = c->d_status;
         a.ncols = ncols;
         a.n = n;
         a.a = c->blocks[j].a;
-        a.mode = (j == nb - 1 ? TCB_LOAD_PHI : 0) | (j == 0 ? (TCB_GEN | TCB_NO_STORE) : 0) |
-                 (tan ? 0 : TCB_NO_TANGENT);
+        a.mode = (j == 0 ? TCB_NO_STORE : 0) | (tan ? 0 : TCB_NO_TANGENT);
         a.wait_limit = c->tc_wait_limit;
         a.barrier_extra = c->tc_barrier_extra;
         CUDA_TRY(c, launch_tcb(a, true, c->tc_ctas_bwd, c->stream));
-        const double by = (j == nb - 1 ? 8.0 : 16.0) + (j ? 16.0 : 0.0) + (j ? 16.0 : 0.0);
+        const double by = 32.0 + (j ? 16.0 : 0.0);
         if ((rc = prof_mark(c, HVP_K_BLOCK_BWD, amps * fl_bwd, amps * by))) return rc;
         ++L;
     }
@@ -621,14 +621,13 @@ int compute_phi_from_uref(hvp_ctx* c, const double* uref) {
         for (int j = 0; j < c->nb; ++j) {
             TcbArgs a{};
             a.ops = c->d_ops + (size_t)j * kOpWords;
-            a.xin = j ? reinterpret_cast<const float4*>(c->tstate[j - 1]) : nullptr;
+            a.xin = reinterpret_cast<const float4*>(j ? c->tstate[j - 1] : c->d_psi0);
             a.xout = reinterpret_cast<float4*>(c->tstate[j]);
-            a.psi1q = reinterpret_cast<const float2*>(c->d_psi1q);
-            a.status = c->d_status;
+                a.status = c->d_status;
             a.ncols = (long long)ns << (n - 5);
             a.n = n;
             a.a = c->blocks[j].a;
-            a.mode = (j == 0 ? TCB_GEN : 0) | TCB_NO_TANGENT;
+            a.mode = TCB_NO_TANGENT;
             CUDA_TRY(c, launch_tcb(a, false, c->tc_ctas_fwd, c->stream));
         }
         CUDA_TRY(c, launch_extract_psi(reinterpret_cast<const float4*>(c->tstate[c->nb - 1]),
@@ -881,6 +880,7 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
         c->tstate.assign(c->nb, nullptr);
         for (int j = 0; j < c->nb; ++j)
             if ((rc = dalloc(c, &c->tstate[j], sbytes))) return rc;
+        if ((rc = dalloc(c, &c->d_psi0, sbytes))) return rc;
     } else if (c->unfused) {
         if ((rc = dalloc(c, &c->d_x, state_elt(c) * dim * ns))) return rc;
     } else {
@@ -972,6 +972,8 @@ int init_impl(hvp_ctx* c, const hvp_config* cfg, const double* psi_1q, const dou
     CUDA_TRY(c, cudaMemcpy(tmp, psi_1q, sizeof(double) * ns * n * 4, cudaMemcpyHostToDevice));
     if (c->dbl) CUDA_TRY(c, cudaMemcpy(c->d_psi1q, tmp, sizeof(double) * ns * n * 4, cudaMemcpyDeviceToDevice));
     else CUDA_TRY(c, launch_psi1q_convert(tmp, (float2*)c->d_psi1q, (size_t)ns * n * 2, c->stream));
+    if (c->tensor)   // the block passes read the product input states like any other block input
+        CUDA_TRY(c, launch_product_states((const float2*)c->d_psi1q, (float4*)c->d_psi0, n, ns, c->stream));
     if (cfg->flags & HVP_PHI_GIVEN) {
         std::vector<int> pos(n);
         if (c->unfused || c->tensor) {

@@ -340,7 +340,55 @@ __global__ void extract_psi_kernel(const float4* __restrict__ x, float2* __restr
     }
 }
 
+// The product input states psi^[0]_s = (x)_q psi_{s,q} (Eq. costHS) as
+// float4 (psi, dpsi = 0), factors multiplied in qubit order.
+__global__ void product_states_kernel(const float2* __restrict__ q1, float4* __restrict__ out, int n, size_t count) {
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = g >> n;
+        const unsigned long long idx = g & ((1ull << n) - 1ull);
+        const float2* f = q1 + s * (size_t)n * 2;
+        float2 a = make_float2(1.f, 0.f);
+        for (int q = 0; q < n; ++q) {
+            const float2 v = __ldg(&f[2 * q + ((idx >> (n - 1 - q)) & 1ull)]);
+            a = make_float2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x);
+        }
+        out[g] = make_float4(a.x, a.y, 0.f, 0.f);
+    }
+}
+
+// The co-states entering the backward sweep, weighted by the overlaps:
+// (w1_s phi_s, w2_s phi_s), w1 = T_s and w2 = Omega_s (or 1 and 0 when null).
+__global__ void weighted_phi_kernel(const float2* __restrict__ phi, const double2* __restrict__ w1,
+                                    const double2* __restrict__ w2, float4* __restrict__ out, int n, size_t count) {
+    for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < count; g += (size_t)gridDim.x * blockDim.x) {
+        const float2 ph = __ldg(&phi[g]);
+        const size_t s = g >> n;
+        float2 a = make_float2(1.f, 0.f), b = make_float2(0.f, 0.f);
+        if (w1) a = make_float2((float)w1[s].x, (float)w1[s].y);
+        if (w2) b = make_float2((float)w2[s].x, (float)w2[s].y);
+        out[g] = make_float4(a.x * ph.x - a.y * ph.y, a.x * ph.y + a.y * ph.x, b.x * ph.x - b.y * ph.y,
+                             b.x * ph.y + b.y * ph.x);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_product_states(const float2* psi1q, float4* out, int n, int ns, cudaStream_t st) {
+    const size_t count = ((size_t)1 << n) * ns;
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    product_states_kernel<<<(int)blocks, 256, 0, st>>>(psi1q, out, n, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_phi(const float2* phi, const double2* w1, const double2* w2, float4* out, int n, int ns,
+                                cudaStream_t st) {
+    const size_t count = ((size_t)1 << n) * ns;
+    size_t blocks = (count + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    weighted_phi_kernel<<<(int)blocks, 256, 0, st>>>(phi, w1, w2, out, n, count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_extract_psi(const float4* x, float2* out, size_t count, cudaStream_t st) {
     size_t blocks = (count + 255) / 256;

@@ -111,9 +111,7 @@ void build_dev_passes(const Plan& plan, std::vector<DevPass>& dp, std::vector<De
 // B^dag]] C with the block environment of the co-states after the update and
 // the forward states at the block's input accumulated into rec.
 enum TcbMode : int {
-    TCB_GEN = 1,       // forward states of the block's input generated (product states)
-    TCB_LOAD_PHI = 2,  // backward: co-states start as (w1 phi, w2 phi)
-    TCB_NO_STORE = 4,  // backward: the updated co-states are not stored (first block)
+    TCB_NO_STORE = 4,    // backward: the updated co-states are not stored (first block)
     TCB_NO_TANGENT = 8,  // the tangent components are zero and stay zero (no GEMM on them)
 };
 
@@ -134,10 +132,6 @@ struct TcbArgs {
     const float4* xin;       // forward: states at the block's input; backward: co-states
     float4* xout;            // forward: states at the block's output; backward: co-states (in place)
     const float4* psi;       // backward: forward states at the block's input
-    const float2* phi;       // backward with TCB_LOAD_PHI: reference states (standard order)
-    const double2* w1;       // with TCB_LOAD_PHI: per-sample weights (T_s), or null for 1
-    const double2* w2;       // per-sample weights (Omega_s), or null for 0
-    const float2* psi1q;     // N_s x n x 2 single-qubit factors (TCB_GEN)
     double* rec;             // backward: FP64 environment records of this block, [CTA][128][128]
     int* status;             // bit 2: a bounded wait gave up
     long long ncols;         // N_s * 2^(n - 5)
@@ -160,6 +154,9 @@ cudaError_t launch_block_prep(const DevBlock* blocks, const DevBlockGate* bg, in
 cudaError_t launch_overlaps(const float4* x, const float2* phi, double* partial, double2* T, double2* Om, int n,
                             int ns, int chunks, cudaStream_t st);
 cudaError_t launch_extract_psi(const float4* x, float2* out, size_t count, cudaStream_t st);
+cudaError_t launch_product_states(const float2* psi1q, float4* out, int n, int ns, cudaStream_t st);
+cudaError_t launch_weighted_phi(const float2* phi, const double2* w1, const double2* w2, float4* out, int n, int ns,
+                                cudaStream_t st);
 
 // Swizzle of shared-memory element indices (16-byte elements): conflict-free
 // 128-bit accesses when no two neighbouring qubits sit on index bits 0..2.

@@ -291,18 +291,6 @@ __device__ __forceinline__ size_t amp_index(long long c, unsigned b, int bl) {
     return (size_t)(((u >> bl) << (bl + 5)) | ((unsigned long long)b << bl) | (u & ((1ull << bl) - 1ull)));
 }
 
-// Product state psi^[0] = (x)_q psi_{s,q} at one amplitude (Eq. costHS).
-__device__ __forceinline__ float2 product_amp(const float2* __restrict__ q1, size_t g, int n) {
-    const size_t s = g >> n;
-    const unsigned long long idx = g & ((1ull << n) - 1ull);
-    const float2* f = q1 + s * (size_t)n * 2;
-    float2 a = make_float2(1.f, 0.f);
-    for (int q = 0; q < n; ++q) {
-        const float2 v = __ldg(&f[2 * q + ((idx >> (n - 1 - q)) & 1ull)]);
-        a = make_float2(a.x * v.x - a.y * v.y, a.x * v.y + a.y * v.x);
-    }
-    return a;
-}
 
 // Power-of-two scale exponent of a column: 2^e > m >= 2^(e-1) for the largest
 // magnitude m (bits of a non-negative float); bounded below so that the
@@ -329,6 +317,98 @@ __device__ __forceinline__ void slice3_pair(float re, float im, uint32_t& p0, ui
 // Rows 4 b + p (p = the four components, four columns per 16-byte row) of a
 // TF32 operand of the environment GEMM: high parts at dst + base, low parts
 // one region further. One copy of this code serves both operands.
+// Offset of column c of block index b in a raw tile: four 4 KB boxes of 8
+// columns (c = 8 g + c'). At bl >= 3 box g row b holds the 8 columns of block
+// index b (128 bytes, 16-byte chunk c' XOR (b mod 8), the TMA's 128-byte
+// swizzle); at bl < 3 box g holds 8 / 2^bl runs of 32 x 2^bl amplitudes in
+// memory order. Either way the 32 block indices of one column are
+// conflict-free for bl = 0 and bl >= 3 (2- and 4-way at bl = 1, 2).
+__device__ __forceinline__ unsigned raw_off(unsigned b, unsigned c, int bl) {
+    const unsigned g = c >> 3, cq = c & 7u;
+    if (bl >= 3) return g * 4096u + b * 128u + ((cq ^ (b & 7u)) << 4);
+    const unsigned pl = 1u << bl;
+    return g * 4096u + (((cq >> bl) * 32u + b) * pl + (cq & (pl - 1u))) * 16u;
+}
+
+// Raw tile loaded by the threads of a role (inputs without a tensor map):
+// the thread's four elements (block index b, columns 4 qd .. 4 qd + 3, zero
+// past the last column) stored at their raw-tile offsets, then its arrival on
+// the slot's barrier. Out of line: the tensor-map path is the usual one.
+__device__ __noinline__ void load_raw_direct(unsigned char* dst, const float4* __restrict__ src, long long c0,
+                                             long long ncols, unsigned qd, unsigned b, int bl, uint64_t* bar) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const unsigned c = 4u * qd + (unsigned)i;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + c < ncols) v = __ldcs(src + amp_index(c0 + c, b, bl));
+        *reinterpret_cast<float4*>(dst + raw_off(b, c, bl)) = v;
+    }
+    mbar_arrive(bar);   // (release: orders the stores above)
+}
+
+// The four TMA box loads of one raw tile (kRawTile bytes expected on bar).
+__device__ __forceinline__ void tma_tile(unsigned char* dst, const CUtensorMap* map, long long c0, int bl,
+                                         uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, kRawTile);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long cg = c0 + 8 * q;
+        if (bl >= 3)
+            tma_load(dst + 4096 * q, map, 0, (int)((cg & ((1ll << bl) - 1)) >> 3), 0, (int)(cg >> bl), bar, true);
+        else
+            tma_load(dst + 4096 * q, map, 0, 0, (int)(cg >> bl), 0, bar, false);
+    }
+}
+// The same out of line. The backward kernel's four roles do not fit the
+// instruction cache together, and it runs faster with its producers' TMA
+// issue and slicing as calls (the forward kernel, with less code, runs
+// faster with them inlined).
+__device__ __noinline__ void tma_tile_call(unsigned char* dst, const CUtensorMap* map, long long c0, int bl,
+                                           uint64_t* bar) {
+    tma_tile(dst, map, c0, bl, bar);
+}
+
+// One producer's part of the X operand of a tile: for each of its four
+// columns c = 4 uq + i (and, with tangents, TN + c) the power-of-two scale
+// from the warp's maximum magnitude (published in cs by lane 0), then the
+// three 8-bit slice pairs of its block-index row, stored in the three slice
+// regions of xb at kb + the column's core-matrix offset.
+__device__ __forceinline__ void slice_cols_body(unsigned char* xb, float* cs, unsigned kb, int uq, int lane,
+                                                bool tangent, const float4 (&xr)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c = 4 * uq + i;
+        const unsigned m0 = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(xr[i].x), fabsf(xr[i].y))));
+        const int e0 = col_exp(m0);
+        const float u0 = pow2f(8 - e0);
+        uint32_t p0, p1, p2;
+        const unsigned o0 = kb + (unsigned)(c & 7) * 16u + (unsigned)(c >> 3) * kSboX;
+        slice3_pair(xr[i].x * u0, xr[i].y * u0, p0, p1, p2);
+        *reinterpret_cast<uint32_t*>(xb + o0) = p0;
+        *reinterpret_cast<uint32_t*>(xb + kXRegion + o0) = p1;
+        *reinterpret_cast<uint32_t*>(xb + 2 * kXRegion + o0) = p2;
+        if (lane == 0) cs[c] = pow2f(e0 - 8);
+        if (tangent) {
+            const int cn = TN + c;
+            const unsigned m1 = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(xr[i].z), fabsf(xr[i].w))));
+            const int e1 = col_exp(m1);
+            const float u1 = pow2f(8 - e1);
+            const unsigned o1 = kb + (unsigned)(cn & 7) * 16u + (unsigned)(cn >> 3) * kSboX;
+            slice3_pair(xr[i].z * u1, xr[i].w * u1, p0, p1, p2);
+            *reinterpret_cast<uint32_t*>(xb + o1) = p0;
+            *reinterpret_cast<uint32_t*>(xb + kXRegion + o1) = p1;
+            *reinterpret_cast<uint32_t*>(xb + 2 * kXRegion + o1) = p2;
+            if (lane == 0) cs[cn] = pow2f(e1 - 8);
+        }
+    }
+}
+// The same out of line, with its inputs by value (the backward kernel).
+__device__ __noinline__ void slice_cols_call(unsigned char* xb, float* cs, unsigned kb, int uq, int lane, bool tangent,
+                                             float4 x0, float4 x1, float4 x2, float4 x3) {
+    const float4 xr[4] = {x0, x1, x2, x3};
+    slice_cols_body(xb, cs, kb, uq, lane, tangent, xr);
+}
+
 __device__ __noinline__ void put_tf32_rows(unsigned char* dst, unsigned base, float4 v0, float4 v1, float4 v2,
                                            float4 v3) {
     const float4 v[4] = {v0, v1, v2, v3};
@@ -381,9 +461,8 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
     if (tid == 0) {
         const unsigned cm = 1u + a.barrier_extra;   // arrivals a commit barrier expects
         // ring slots: one arrival (the TMA issuer, expecting the bytes) or,
-        // for inputs loaded or computed by the threads, one per producer
-        const bool xgen = (!BWD && (a.mode & TCB_GEN)) || (BWD && (a.mode & TCB_LOAD_PHI)) || !a.tma_x;
-        const bool pgen = (BWD && (a.mode & TCB_GEN)) || !a.tma_p;
+        // for inputs loaded by the threads (no tensor map), one per thread of the role
+        const bool xgen = !a.tma_x, pgen = !a.tma_p;
         const unsigned rx = xgen ? 256u : 1u, rp = pgen ? 256u : 1u;
         const unsigned r2 = RX > 2 ? rx : rp, r3 = RX > 3 ? rx : rp;
         const unsigned counts[B_COUNT] = {256u, 256u, cm, cm, cm, cm, 256u, 256u, 256u, 256u,
@@ -437,23 +516,11 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
     const int qd = warp < 8 ? warp : warp - 8;
     const bool leader = tid == 0 || tid == 256;
     bool bad = false;
-    // Raw tiles: four 4 KB boxes of 8 columns (c = 8 g + c'). Block bits at
-    // bl >= 3: box g row b = the 8 columns of block index b (128 bytes,
-    // 16-byte chunk c' XOR (b mod 8), the TMA's 128-byte swizzle); bl < 3:
-    // box g holds 8 / 2^bl runs of 32 x 2^bl amplitudes in memory order.
-    // Either way the 32 block indices of one column are conflict-free
-    // for bl = 0 and bl >= 3 (2- and 4-way at bl = 1, 2).
-    auto tile_off = [&](unsigned b, unsigned c) -> unsigned {
-        const unsigned g = c >> 3, cq = c & 7u;
-        if (bl >= 3) return g * 4096u + b * 128u + ((cq ^ (b & 7u)) << 4);
-        const unsigned pl = 1u << bl;
-        return g * 4096u + (((cq >> bl) * 32u + b) * pl + (cq & (pl - 1u))) * 16u;
-    };
+    auto tile_off = [&](unsigned b, unsigned c) -> unsigned { return raw_off(b, c, bl); };
     // Loads of local tile j (global tile blockIdx.x + j gridDim.x) into
     // ring slot s: one thread issues the four TMA box loads (expecting
-    // their bytes on the slot's barrier); computed inputs (product states,
-    // weighted reference states), and inputs without a tensor map, are
-    // loaded or computed by every thread for its own elements instead,
+    // their bytes on the slot's barrier); inputs without a tensor map are
+    // loaded by every thread of the role for its own elements instead,
     // each arriving on the barrier. Nothing is issued for tiles past the
     // end (no one waits for them).
     long long x_issued = 0, x_taken = 0, p_issued = 0, p_taken = 0;   // local tiles
@@ -462,49 +529,16 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         if (tile >= ntiles) return;
         (psi ? p_issued : x_issued) = j + 1;
         unsigned char* dst = ring + (unsigned)s * kRawTile;
-        const bool gen = psi ? (a.mode & TCB_GEN) != 0
-                             : (!BWD && (a.mode & TCB_GEN)) || (BWD && (a.mode & TCB_LOAD_PHI));
         const long long c0 = tile * TN;
-        if (!gen && (psi ? a.tma_p : a.tma_x)) {
+        if (psi ? a.tma_p : a.tma_x) {
             if (leader) {   // (the role's reads of the slot precede its barrier before this refill)
-                mbar_arrive_expect_tx(&bars[B_RING0 + s], kRawTile);
                 const CUtensorMap* map = psi ? &a.tm_p : &a.tm_x;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const long long cg = c0 + 8 * q;
-                    if (bl >= 3)
-                        tma_load(dst + 4096 * q, map, 0, (int)((cg & ((1ll << bl) - 1)) >> 3), 0, (int)(cg >> bl),
-                                 &bars[B_RING0 + s], true);
-                    else
-                        tma_load(dst + 4096 * q, map, 0, 0, (int)(cg >> bl), 0, &bars[B_RING0 + s], false);
-                }
+                if constexpr (BWD) tma_tile_call(dst, map, c0, bl, &bars[B_RING0 + s]);
+                else tma_tile(dst, map, c0, bl, &bars[B_RING0 + s]);
             }
             return;
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const unsigned c = (unsigned)(4 * qd + i);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (c0 + c < ncols) {
-                const size_t gi = amp_index(c0 + c, (unsigned)lane, bl);
-                if (!gen) {
-                    v = __ldcs((psi ? a.psi : a.xin) + gi);
-                } else if (psi || !BWD) {
-                    const float2 p = product_amp(a.psi1q, gi, n);
-                    v = make_float4(p.x, p.y, 0.f, 0.f);
-                } else {
-                    const float2 ph = __ldg(&a.phi[gi]);
-                    const size_t smp = gi >> n;
-                    float2 w1 = make_float2(1.f, 0.f), w2 = make_float2(0.f, 0.f);
-                    if (a.w1) w1 = make_float2((float)a.w1[smp].x, (float)a.w1[smp].y);
-                    if (a.w2) w2 = make_float2((float)a.w2[smp].x, (float)a.w2[smp].y);
-                    v = make_float4(w1.x * ph.x - w1.y * ph.y, w1.x * ph.y + w1.y * ph.x,
-                                    w2.x * ph.x - w2.y * ph.y, w2.x * ph.y + w2.y * ph.x);
-                }
-            }
-            *reinterpret_cast<float4*>(dst + tile_off((unsigned)lane, c)) = v;
-        }
-        mbar_arrive(&bars[B_RING0 + s]);   // (release: orders the stores above)
+        load_raw_direct(dst, psi ? a.psi : a.xin, c0, ncols, (unsigned)qd, (unsigned)lane, bl, &bars[B_RING0 + s]);
     };
     auto issue_x = [&](long long j) { issue(j, (int)(j % RX), false); };
     auto issue_p = [&](long long j) { issue(j, RX + (int)(j % (RP > 0 ? RP : 1)), true); };
@@ -611,33 +645,8 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             unsigned char* xb = xslots + sg * kXSlot;
             float* cs = csc + (int)(j & 3) * NE;
             const unsigned kb = (ub >> 2) * kLboX + (ub & 3u) * 4u;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int c = 4 * uq + i;
-                const unsigned m0 = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(xr[i].x), fabsf(xr[i].y))));
-                const int e0 = col_exp(m0);
-                const float u0 = pow2f(8 - e0);
-                uint32_t p0, p1, p2;
-                const unsigned o0 = kb + (unsigned)(c & 7) * 16u + (unsigned)(c >> 3) * kSboX;
-                slice3_pair(xr[i].x * u0, xr[i].y * u0, p0, p1, p2);
-                *reinterpret_cast<uint32_t*>(xb + o0) = p0;
-                *reinterpret_cast<uint32_t*>(xb + kXRegion + o0) = p1;
-                *reinterpret_cast<uint32_t*>(xb + 2 * kXRegion + o0) = p2;
-                if (lane == 0) cs[c] = pow2f(e0 - 8);
-                if (tangent) {
-                    const int cn = TN + c;
-                    const unsigned m1 =
-                        __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(xr[i].z), fabsf(xr[i].w))));
-                    const int e1 = col_exp(m1);
-                    const float u1 = pow2f(8 - e1);
-                    const unsigned o1 = kb + (unsigned)(cn & 7) * 16u + (unsigned)(cn >> 3) * kSboX;
-                    slice3_pair(xr[i].z * u1, xr[i].w * u1, p0, p1, p2);
-                    *reinterpret_cast<uint32_t*>(xb + o1) = p0;
-                    *reinterpret_cast<uint32_t*>(xb + kXRegion + o1) = p1;
-                    *reinterpret_cast<uint32_t*>(xb + 2 * kXRegion + o1) = p2;
-                    if (lane == 0) cs[cn] = pow2f(e1 - 8);
-                }
-            }
+            if constexpr (BWD) slice_cols_call(xb, cs, kb, uq, lane, tangent, xr[0], xr[1], xr[2], xr[3]);
+            else slice_cols_body(xb, cs, kb, uq, lane, tangent, xr);
             if (lane == 0) mbar_arrive(&bars[B_SCALES0 + (int)(j & 3)]);
             fence_async_smem();
             mbar_arrive(&bars[B_FULL0 + sg]);
@@ -962,10 +971,8 @@ cudaError_t launch_tcb(const TcbArgs& args, bool bwd, int ctas, cudaStream_t st)
     if (args.n < 5 || args.a < 0 || args.a + 5 > args.n || ctas < 1) return cudaErrorInvalidValue;
     TcbArgs a = args;
     const int bl = a.n - a.a - 5;
-    const bool xgen = (!bwd && (a.mode & TCB_GEN)) || (bwd && (a.mode & TCB_LOAD_PHI));
-    const bool pgen = !bwd || (a.mode & TCB_GEN);
-    a.tma_x = !xgen && encode_state_map(&a.tm_x, a.xin, bl, a.ncols);
-    a.tma_p = !pgen && encode_state_map(&a.tm_p, a.psi, bl, a.ncols);
+    a.tma_x = encode_state_map(&a.tm_x, a.xin, bl, a.ncols);
+    a.tma_p = bwd && encode_state_map(&a.tm_p, a.psi, bl, a.ncols);
     const unsigned smem = launch_smem(bwd);
     if (bwd) tcb_kernel<true><<<ctas, kT + 32, smem, st>>>(a);
     else tcb_kernel<false><<<ctas, kT + 32, smem, st>>>(a);
