@@ -314,9 +314,6 @@ __device__ __forceinline__ void slice3_pair(float re, float im, uint32_t& p0, ui
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(p2) : "f"(i2), "f"(r2));
 }
 
-// Rows 4 b + p (p = the four components, four columns per 16-byte row) of a
-// TF32 operand of the environment GEMM: high parts at dst + base, low parts
-// one region further. One copy of this code serves both operands.
 // Offset of column c of block index b in a raw tile: four 4 KB boxes of 8
 // columns (c = 8 g + c'). At bl >= 3 box g row b holds the 8 columns of block
 // index b (128 bytes, 16-byte chunk c' XOR (b mod 8), the TMA's 128-byte
@@ -409,6 +406,9 @@ __device__ __noinline__ void slice_cols_call(unsigned char* xb, float* cs, unsig
     slice_cols_body(xb, cs, kb, uq, lane, tangent, xr);
 }
 
+// Rows 4 b + p (p = the four components, four columns per 16-byte row) of a
+// TF32 operand of the environment GEMM: high parts at dst + base, low parts
+// one region further. One copy of this code serves both operands.
 __device__ __noinline__ void put_tf32_rows(unsigned char* dst, unsigned base, float4 v0, float4 v1, float4 v2,
                                            float4 v3) {
     const float4 v[4] = {v0, v1, v2, v3};
