@@ -64,7 +64,9 @@ extern "C" {
 #define HVP_RIEMANNIAN 1  /* grad/hvp outputs are the Riemannian forms (App. F) */
 #define HVP_PHI_GIVEN 2   /* ref_data holds phi_s (N_s x 2^n) instead of U_ref */
 #define HVP_UNFUSED 4     /* one kernel launch per gate (the plain schedule)    */
-#define HVP_NO_GRAPH 8    /* launch kernels directly instead of a CUDA graph   */
+#define HVP_NO_GRAPH 8    /* launch kernels directly instead of a CUDA graph
+                             (each pass is then also an NVTX range, named
+                             with its index; every call is one)            */
 #define HVP_AUTOTUNE 16   /* time the window/threads/arithmetic candidates at
                              hvp_init and keep the fastest (see hvp_plan_info) */
 #define HVP_FROBENIUS 32  /* loss, gradient and HVP of the sampled Frobenius
@@ -334,8 +336,8 @@ int hvp_profile(hvp_ctx *ctx, const double *G_dev, const double *V_dev, int max_
  * The call is synchronous: it copies its small tables from host memory into
  * the array, enqueues its kernels on `stream`, reads back a status word and
  * waits for the stream before it returns.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture. Every call reuses the same array, so
+ * The first call on a device also looks up the array's device address.
+ * Every call reuses the same array, so
  * calls that overlap on the GPU (other threads, other streams) race; serialise
  * them. */
 #define HVP_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -30,6 +30,7 @@
 
 #include "../../include/hvp.h"
 #include "internal.h"
+#include "nvtx.h"
 
 using namespace hvp;
 
@@ -218,6 +219,7 @@ const void* boundary_in(hvp_ctx* c, int j) {   // forward states after pass j-1
 // cache, backward passes read it).
 int tiled_pass(hvp_ctx* c, int p, int mode, const void* xin, void* xout, bool tan, int ld_out, int st_out,
                const void* mats, const void* phi, bool cached = false) {
+    NvtxRange range((mode & M_BWD) ? ((mode & M_FWD) ? "turnaround pass" : "backward pass") : "forward pass", p);
     TiledArgs a{};
     a.pass = c->d_pass + p;
     a.gates = c->d_gates;
@@ -338,6 +340,7 @@ int enqueue_unfused(hvp_ctx* c, bool tan, int* launches) {
     if ((rc = prof_mark(c, HVP_K_GATE_INIT, 0.0, amps * elt))) return rc;
     ++L;
     for (int k = 0; k < K; ++k) {
+        NvtxRange range("forward gate", k);
         CUDA_TRY(c, unfused_fwd_gate(c->dbl, c->d_mats, k, c->plan.first_qubit[k], c->d_x, n, ns, tan, c->stream));
         if ((rc = prof_mark(c, HVP_K_GATE_FWD, amps * (tan ? 96.0 : 32.0), 2 * amps * elt))) return rc;
         ++L;
@@ -346,6 +349,7 @@ int enqueue_unfused(hvp_ctx* c, bool tan, int* launches) {
     if ((rc = prof_mark(c, HVP_K_GATE_PHI, 0.0, amps * (cb + elt)))) return rc;
     ++L;
     for (int k = K - 1; k >= 0; --k) {
+        NvtxRange range("backward gate", k);
         CUDA_TRY(c, unfused_bwd_gate(c->dbl, c->d_mats, k, c->plan.first_qubit[k], c->d_x, c->d_co, c->d_partial, n,
                                      ns, c->cx_count, tan, c->stream));
         if ((rc = prof_mark(c, HVP_K_GATE_BWD, amps * (tan ? 288.0 : 96.0), 4 * amps * elt))) return rc;
@@ -358,6 +362,7 @@ int enqueue_unfused(hvp_ctx* c, bool tan, int* launches) {
 // One pass of the two-direction schedule (both directions' tangents in one
 // sweep, forward cache of 24 bytes per amplitude per gate).
 int pair_pass(hvp_ctx* c, int p, int mode) {
+    NvtxRange range((mode & M_BWD) ? ((mode & M_FWD) ? "turnaround pass" : "backward pass") : "forward pass", p);
     TiledArgs a{};
     a.pass = c->d_pass + p;
     a.gates = c->d_gates;
@@ -484,6 +489,7 @@ int enqueue_tensor(hvp_ctx* c, bool tan) {
         a.mode = tan ? 0 : TCB_NO_TANGENT;
         a.wait_limit = c->tc_wait_limit;
         a.barrier_extra = c->tc_barrier_extra;
+        NvtxRange range("forward block", j);
         CUDA_TRY(c, launch_tcb(a, false, c->tc_ctas_fwd, c->stream));
         if ((rc = prof_mark(c, HVP_K_BLOCK_FWD, amps * fl_fwd, amps * 32.0))) return rc;
         ++L;
@@ -512,6 +518,7 @@ int enqueue_tensor(hvp_ctx* c, bool tan) {
         a.mode = (j == 0 ? TCB_NO_STORE : 0) | (tan ? 0 : TCB_NO_TANGENT);
         a.wait_limit = c->tc_wait_limit;
         a.barrier_extra = c->tc_barrier_extra;
+        NvtxRange range("backward block", j);
         CUDA_TRY(c, launch_tcb(a, true, c->tc_ctas_bwd, c->stream));
         const double by = 32.0 + (j ? 16.0 : 0.0);
         if ((rc = prof_mark(c, HVP_K_BLOCK_BWD, amps * fl_bwd, amps * by))) return rc;
@@ -623,7 +630,7 @@ int compute_phi_from_uref(hvp_ctx* c, const double* uref) {
             a.ops = c->d_ops + (size_t)j * kOpWords;
             a.xin = reinterpret_cast<const float4*>(j ? c->tstate[j - 1] : c->d_psi0);
             a.xout = reinterpret_cast<float4*>(c->tstate[j]);
-                a.status = c->d_status;
+            a.status = c->d_status;
             a.ncols = (long long)ns << (n - 5);
             a.n = n;
             a.a = c->blocks[j].a;
@@ -1044,6 +1051,7 @@ int hvp_internal_copy_phi(hvp_ctx* c, void* dst, size_t bytes) {
 extern "C" {
 
 int hvp_init(hvp_ctx** out, const hvp_config* cfg, const double* psi_1q, const double* ref_data) {
+    NvtxRange range("hvp_init");
     if (!out) return fail(nullptr, HVP_EINVAL, "hvp_init: out is NULL");
     *out = nullptr;
     hvp_ctx* c = new (std::nothrow) hvp_ctx();
@@ -1060,6 +1068,7 @@ int hvp_init(hvp_ctx** out, const hvp_config* cfg, const double* psi_1q, const d
 
 int hvp_init_batch(hvp_ctx** out, int n_circuits, const hvp_config* cfgs, const double* const* psi_1q,
                    const double* const* ref_data) {
+    NvtxRange range("hvp_init_batch");
     if (!out) return fail(nullptr, HVP_EINVAL, "hvp_init_batch: out is NULL");
     *out = nullptr;
     if (n_circuits < 1 || !cfgs || !psi_1q || !ref_data)
@@ -1143,16 +1152,19 @@ int hvp_init_batch(hvp_ctx** out, int n_circuits, const hvp_config* cfgs, const 
 }
 
 int hvp_loss_grad(hvp_ctx* ctx, const double* G, double* loss, double* grad) {
+    NvtxRange range("hvp_loss_grad");
     return call_impl(ctx, G, nullptr, loss, grad, nullptr);
 }
 
 int hvp_hvp(hvp_ctx* ctx, const double* G, const double* V, double* loss, double* grad, double* hvp) {
+    NvtxRange range("hvp_hvp");
     if (ctx && !V) return fail(ctx, HVP_EINVAL, "V is NULL");
     return call_impl(ctx, G, V, loss, grad, hvp);
 }
 
 int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* loss_dev, double* grad_dev,
                 double* hvp_dev) {
+    NvtxRange range("hvp_hvp_dev");
     if (!c) return HVP_EINVAL;
     if (!G_dev) return fail(c, HVP_EINVAL, "G_dev is NULL");
     if (c->batch) {
@@ -1179,6 +1191,7 @@ int hvp_hvp_dev(hvp_ctx* c, const double* G_dev, const double* V_dev, double* lo
 
 int hvp_hvp_multi_dev(hvp_ctx* c, const double* G_dev, int n_dir, const double* V_dev, double* loss_dev,
                       double* grad_dev, double* hvp_dev) {
+    NvtxRange range("hvp_hvp_multi_dev");
     if (!c) return HVP_EINVAL;
     if (!G_dev || !V_dev || n_dir < 1) return fail(c, HVP_EINVAL, "hvp_hvp_multi_dev: NULL input or n_dir < 1");
     if (c->batch) return fail(c, HVP_EINVAL, "hvp_hvp_multi_dev: not available for a batch context");
@@ -1221,6 +1234,7 @@ int hvp_hvp_multi_dev(hvp_ctx* c, const double* G_dev, int n_dir, const double* 
 
 int hvp_hvp_multi(hvp_ctx* c, const double* G, int n_dir, const double* V, double* loss, double* grad,
                   double* hvp) {
+    NvtxRange range("hvp_hvp_multi");
     if (!c) return HVP_EINVAL;
     if (!G || !V || n_dir < 1) return fail(c, HVP_EINVAL, "hvp_hvp_multi: NULL input or n_dir < 1");
     if (c->batch) return fail(c, HVP_EINVAL, "hvp_hvp_multi: not available for a batch context");
@@ -1274,6 +1288,7 @@ int hvp_hvp_multi(hvp_ctx* c, const double* G, int n_dir, const double* V, doubl
 
 int hvp_profile(hvp_ctx* c, const double* G_dev, const double* V_dev, int max_launches, float* ms, int* kind,
                 double* flops, double* bytes) {
+    NvtxRange range("hvp_profile");
     if (!c || !G_dev || max_launches < 0) return HVP_EINVAL;
     if (c->batch) return fail(c, HVP_EINVAL, "hvp_profile: not available for a batch context");
     const size_t n32 = 32 * c->n_user();

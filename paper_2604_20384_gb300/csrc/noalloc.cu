@@ -16,6 +16,7 @@
 
 #include "../../include/hvp.h"
 #include "internal.h"
+#include "nvtx.h"
 
 namespace hvp {
 namespace {
@@ -81,6 +82,7 @@ using namespace hvp;
 extern "C" int hvp_hvp_noalloc(int n, int n_layers, int n_samples, const double* psi_1q_dev,
                                const double* phi_dev, const double* G_dev, const double* V_dev,
                                double* loss_dev, double* grad_dev, double* hvp_dev, void* stream) {
+    NvtxRange range("hvp_hvp_noalloc");
     if (!psi_1q_dev || !phi_dev || !G_dev) return err(HVP_EINVAL, "hvp_hvp_noalloc: NULL input pointer");
     if (n < 2 || n > 12) return err(HVP_EINVAL, "hvp_hvp_noalloc: n must be in [2, 12]");
     if (n_layers < 1 || n_samples < 1) return err(HVP_EINVAL, "hvp_hvp_noalloc: n_layers and n_samples must be >= 1");

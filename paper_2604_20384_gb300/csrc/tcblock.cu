@@ -38,11 +38,16 @@
 // record every 64 such pairs, so the truncating accumulation spans two
 // tiles (24 MMAs).
 //
-// Pipeline. One CTA per SM; warps 0-7 load, slice and stage tiles and run the
-// epilogue, warp 8 owns TMEM and its first lane issues every MMA. A tile's
-// global loads are issued one full iteration before the tile is sliced, its
-// slices staged one iteration before its MMAs. Forward, two accumulator
-// buffers let the MMAs of tile i + 1 run during the epilogue of tile i;
+// Pipeline. One CTA per SM, 17 warps: warps 0-7 (producers) slice the X
+// tiles and, backward, read the environment; warps 8-15 (epilogue) combine
+// the accumulators, store the tile and, backward, write the environment
+// GEMM's TF32 operands; warp 16 owns TMEM, and its first lane issues every
+// MMA and every TMA load of the input ring (four 16 KB slots: forward four X
+// tiles, backward two X and two forward-state tiles), refilling a slot once
+// the barrier its readers arrive on (FULL, CREADY) shows that they are done
+// with it. A tile's slices are staged one iteration before its MMAs.
+// Forward, two accumulator buffers let the MMAs of tile i + 1 run during the
+// epilogue of tile i;
 // backward (one accumulator buffer beside the environment), the environment
 // MMAs of tile i - 1 are issued after the update MMAs of tile i and fill the
 // tensor pipe while the epilogue of tile i runs. Every wait on an mbarrier is
@@ -356,15 +361,6 @@ __device__ __forceinline__ void tma_tile(unsigned char* dst, const CUtensorMap* 
             tma_load(dst + 4096 * q, map, 0, 0, (int)(cg >> bl), 0, bar, false);
     }
 }
-// The same out of line. The backward kernel's four roles do not fit the
-// instruction cache together, and it runs faster with its producers' TMA
-// issue and slicing as calls (the forward kernel, with less code, runs
-// faster with them inlined).
-__device__ __noinline__ void tma_tile_call(unsigned char* dst, const CUtensorMap* map, long long c0, int bl,
-                                           uint64_t* bar) {
-    tma_tile(dst, map, c0, bl, bar);
-}
-
 // One producer's part of the X operand of a tile: for each of its four
 // columns c = 4 uq + i (and, with tangents, TN + c) the power-of-two scale
 // from the warp's maximum magnitude (published in cs by lane 0), then the
@@ -399,7 +395,10 @@ __device__ __forceinline__ void slice_cols_body(unsigned char* xb, float* cs, un
         }
     }
 }
-// The same out of line, with its inputs by value (the backward kernel).
+// The same out of line, with its inputs by value. The backward kernel's
+// four roles do not fit the instruction cache together, and it runs faster
+// with its producers' slicing as a call (the forward kernel, with less code,
+// runs faster with it inlined).
 __device__ __noinline__ void slice_cols_call(unsigned char* xb, float* cs, unsigned kb, int uq, int lane, bool tangent,
                                              float4 x0, float4 x1, float4 x2, float4 x3) {
     const float4 xr[4] = {x0, x1, x2, x3};
@@ -509,44 +508,48 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
     };
 
     // ------------------------------------------------------------ input ring
-    // Used by the producers (X) and, backward, by the epilogue (Psi): a
+    // Read by the producers (X) and, backward, by the epilogue (Psi): a
     // worker thread's elements are block index lane, columns 4 qd .. 4 qd + 3
-    // (qd its warp's column quad); the role's first thread issues the TMA
-    // loads.
+    // (qd its warp's column quad).
     const int qd = warp < 8 ? warp : warp - 8;
-    const bool leader = tid == 0 || tid == 256;
     bool bad = false;
     auto tile_off = [&](unsigned b, unsigned c) -> unsigned { return raw_off(b, c, bl); };
-    // Loads of local tile j (global tile blockIdx.x + j gridDim.x) into
-    // ring slot s: one thread issues the four TMA box loads (expecting
-    // their bytes on the slot's barrier); inputs without a tensor map are
-    // loaded by every thread of the role for its own elements instead,
-    // each arriving on the barrier. Nothing is issued for tiles past the
-    // end (no one waits for them).
-    long long x_issued = 0, x_taken = 0, p_issued = 0, p_taken = 0;   // local tiles
-    auto issue = [&](long long j, int s, bool psi) {
+    // Loads of local tile j (global tile blockIdx.x + j gridDim.x) into its
+    // ring slot (X: j mod RX; Psi: RX + j mod RP). With a tensor map the MMA
+    // warp's issuing lane loads the ring (issue_tma): the first tiles at the
+    // start, then each X slot again once every producer has staged the tile
+    // it held (FULL), each Psi slot once every epilogue thread has staged
+    // its forward states (CREADY), so that no worker thread issues copies.
+    // Without one, the role's threads load their own elements when the slot
+    // is free (after the role's barrier), each arriving on the slot's
+    // barrier. Nothing is issued for tiles past the end (no one waits for
+    // them).
+    long long x_issued = 0, p_issued = 0;   // local tiles issued by the MMA lane
+    auto issue_tma = [&](long long j, bool psi) {
         const long long tile = (long long)blockIdx.x + j * g;
         if (tile >= ntiles) return;
+        const int s = psi ? RX + (int)(j % (RP > 0 ? RP : 1)) : (int)(j % RX);
         (psi ? p_issued : x_issued) = j + 1;
         unsigned char* dst = ring + (unsigned)s * kRawTile;
-        const long long c0 = tile * TN;
-        if (psi ? a.tma_p : a.tma_x) {
-            if (leader) {   // (the role's reads of the slot precede its barrier before this refill)
-                const CUtensorMap* map = psi ? &a.tm_p : &a.tm_x;
-                if constexpr (BWD) tma_tile_call(dst, map, c0, bl, &bars[B_RING0 + s]);
-                else tma_tile(dst, map, c0, bl, &bars[B_RING0 + s]);
-            }
-            return;
-        }
-        load_raw_direct(dst, psi ? a.psi : a.xin, c0, ncols, (unsigned)qd, (unsigned)lane, bl, &bars[B_RING0 + s]);
+        const CUtensorMap* map = psi ? &a.tm_p : &a.tm_x;
+        tma_tile(dst, map, tile * TN, bl, &bars[B_RING0 + s]);
     };
-    auto issue_x = [&](long long j) { issue(j, (int)(j % RX), false); };
-    auto issue_p = [&](long long j) { issue(j, RX + (int)(j % (RP > 0 ? RP : 1)), true); };
+    auto issue_direct = [&](long long j, int s, bool psi) {
+        const long long tile = (long long)blockIdx.x + j * g;
+        if (tile >= ntiles) return;
+        load_raw_direct(ring + (unsigned)s * kRawTile, psi ? a.psi : a.xin, tile * TN, ncols, (unsigned)qd,
+                        (unsigned)lane, bl, &bars[B_RING0 + s]);
+    };
+    auto issue_x = [&](long long j) {
+        if (!a.tma_x) issue_direct(j, (int)(j % RX), false);
+    };
+    auto issue_p = [&](long long j) {
+        if (!a.tma_p) issue_direct(j, RX + (int)(j % (RP > 0 ? RP : 1)), true);
+    };
     // The thread's four raw values of local tile j (zero past the last
     // column), once the slot is full.
-    auto take = [&](long long j, int s, int uses, bool psi, float4 (&v)[4]) {
-        if (wait(B_RING0 + s, (unsigned)(uses & 1))) (psi ? p_taken : x_taken) = j + 1;
-        else bad = true;
+    auto take = [&](long long j, int s, int uses, float4 (&v)[4]) {
+        if (!wait(B_RING0 + s, (unsigned)(uses & 1))) bad = true;
         const unsigned char* src = ring + (unsigned)s * kRawTile;
         const long long c0 = ((long long)blockIdx.x + j * g) * TN;
 #pragma unroll
@@ -557,9 +560,9 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             if (!tangent) { v[i].z = 0.f; v[i].w = 0.f; }
         }
     };
-    // No copy into shared memory outlives the CTA: after a failed wait,
-    // tiles issued but not taken are waited for (bounded, regardless of the
-    // stop flag).
+    // No copy into shared memory outlives the CTA: the MMA lane waits for its
+    // last copy into each ring slot (bounded, regardless of the stop flag);
+    // every earlier copy into the slot was taken before the next was issued.
     auto settle = [&](long long from, long long to, int base, int depth) {
         for (long long q = from; q < to; ++q)
             for (unsigned k = 0; k < kSettleLimit; ++k)
@@ -590,16 +593,23 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             };
             // the environment of tile j once its co-states and forward states are staged
             auto env_of = [&](long long j) -> bool {
-                if (!wait(B_CREADY, (unsigned)(j & 1)) || !wait(B_PREADY, (unsigned)(j & 1))) return false;
+                if (!wait(B_CREADY, (unsigned)(j & 1))) return false;
+                if (a.tma_p) issue_tma(j + RP, true);   // every epilogue thread has read Psi slot j mod RP
+                if (!wait(B_PREADY, (unsigned)(j & 1))) return false;
                 tc_fence_after();
                 env((j & 1) != 0);   // odd tiles add onto the even tile before them
                 return true;
             };
+            if (a.tma_x)   // the ring's first tiles
+                for (int q = 0; q < RX; ++q) issue_tma(q, false);
+            if (BWD && a.tma_p)
+                for (int q = 0; q < RP; ++q) issue_tma(q, true);
             bool issued = false, ok = true;
             long long i = 0;
             for (long long tile = blockIdx.x; tile < ntiles; tile += g, ++i) {
                 const int sg = (int)(i & 1), ab = NB == 2 ? sg : 0;
                 if (!wait(B_FULL0 + sg, (unsigned)((i >> 1) & 1))) { ok = false; break; }
+                if (a.tma_x) issue_tma(i + RX, false);   // every producer has read X slot i mod RX
                 if (i >= NB && !wait(B_FREE0 + ab, (unsigned)((i / NB - 1) & 1))) { ok = false; break; }
                 tc_fence_after();
                 // D = A X: levels 0..2 of slice products (i + j = level), 4 K-steps of 16.
@@ -626,6 +636,8 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 for (unsigned k = 0; k < kWaitLimit; ++k)
                     if (mbar_try(&bars[B_DRAIN], 0u)) break;
             }
+            if (a.tma_x) settle(x_issued > RX ? x_issued - RX : 0, x_issued, 0, RX);
+            if (BWD && a.tma_p) settle(p_issued > RP ? p_issued - RP : 0, p_issued, RX, RP > 0 ? RP : 1);
         }
         __syncwarp();
     } else if (producer) {
@@ -641,7 +653,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         // has read it.)
         auto produce_x = [&](long long j, int sg) {
             float4 xr[4];
-            take(j, (int)(j % RX), (int)(j / RX), false, xr);
+            take(j, (int)(j % RX), (int)(j / RX), xr);
             unsigned char* xb = xslots + sg * kXSlot;
             float* cs = csc + (int)(j & 3) * NE;
             const unsigned kb = (ub >> 2) * kLboX + (ub & 3u) * 4u;
@@ -765,7 +777,6 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             double* dst = a.rec + (size_t)blockIdx.x * 16384 + (size_t)row * 128 + 64 * (warp >> 2);
             for (int i = 0; i < 64; ++i) dst[i] = 0.0;
         }
-        settle(x_taken, x_issued, 0, RX);
     } else {
         // ------------------------------------------------------------ epilogue
         // Thread = TMEM lane = operator row. Rows 0-63 (warps with w % 4 < 2)
@@ -830,7 +841,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         auto produce_psi = [&](long long j) {
             if constexpr (BWD) {
                 float4 v[4];
-                take(j, RX + (int)(j % RP), (int)(j / RP), true, v);
+                take(j, RX + (int)(j % RP), (int)(j / RP), v);
                 put_tf32_rows(psislots, (unsigned)qd * kLboE + ((unsigned)lane >> 1) * kSboE + ((unsigned)lane & 1u) * 64u,
                               v[0], v[1], v[2], v[3]);
                 fence_async_smem();
@@ -891,7 +902,6 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             group_sync(2);   // the staging tile is reused by the next tile
             if (BWD && !bad) issue_p(j + RP);   // every epilogue thread has read its forward states
         }
-        if (BWD) settle(p_taken, p_issued, RX, RP > 0 ? RP : 1);
     }
     tc_fence_before();
     __syncthreads();
