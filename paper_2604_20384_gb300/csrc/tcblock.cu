@@ -405,6 +405,20 @@ __device__ __noinline__ void slice_cols_call(unsigned char* xb, float* cs, unsig
     slice_cols_body(xb, cs, kb, uq, lane, tangent, xr);
 }
 
+// The retry loop of a bounded wait, out of line (the first try stays inline):
+// polls until the phase completes, the stop flag rises or the limit runs
+// out, which raises the stop flag and sets bit 2 of *status.
+__device__ __noinline__ bool wait_retry(uint64_t* bar, unsigned par, volatile unsigned* ctl, unsigned limit,
+                                        int* status) {
+    for (unsigned i = 0; i < limit; ++i) {
+        if (mbar_try(bar, par)) return true;
+        if ((i & 255u) == 255u && ctl[1]) return false;
+    }
+    ctl[1] = 1u;
+    atomicOr(status, 2);
+    return false;
+}
+
 // Rows 4 b + p (p = the four components, four columns per 16-byte row) of a
 // TF32 operand of the environment GEMM: high parts at dst + base, low parts
 // one region further. One copy of this code serves both operands.
@@ -498,13 +512,18 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
     // returns at once, so all roles leave their loops.
     auto wait = [&](int b, unsigned par) -> bool {
         if (ctl[1]) return false;
-        for (unsigned i = 0; i < limit; ++i) {
+        if constexpr (BWD) {   // (less code: the backward kernel overflows the instruction cache)
             if (mbar_try(&bars[b], par)) return true;
-            if ((i & 255u) == 255u && ctl[1]) return false;
+            return wait_retry(&bars[b], par, ctl, limit, a.status);
+        } else {
+            for (unsigned i = 0; i < limit; ++i) {
+                if (mbar_try(&bars[b], par)) return true;
+                if ((i & 255u) == 255u && ctl[1]) return false;
+            }
+            ctl[1] = 1u;
+            atomicOr(a.status, 2);
+            return false;
         }
-        ctl[1] = 1u;
-        atomicOr(a.status, 2);
-        return false;
     };
 
     // ------------------------------------------------------------ input ring
