@@ -399,10 +399,11 @@ __device__ __forceinline__ void slice_cols_body(unsigned char* xb, float* cs, un
 // four roles do not fit the instruction cache together, and it runs faster
 // with its producers' slicing as a call (the forward kernel, with less code,
 // runs faster with it inlined).
-__device__ __noinline__ void slice_cols_call(unsigned char* xb, float* cs, unsigned kb, int uq, int lane, bool tangent,
+template <bool TAN>
+__device__ __noinline__ void slice_cols_call(unsigned char* xb, float* cs, unsigned kb, int uq, int lane,
                                              float4 x0, float4 x1, float4 x2, float4 x3) {
     const float4 xr[4] = {x0, x1, x2, x3};
-    slice_cols_body(xb, cs, kb, uq, lane, tangent, xr);
+    slice_cols_body(xb, cs, kb, uq, lane, TAN, xr);
 }
 
 // The retry loop of a bounded wait, out of line (the first try stays inline):
@@ -439,7 +440,7 @@ __device__ __noinline__ void put_tf32_rows(unsigned char* dst, unsigned base, fl
     }
 }
 
-template <bool BWD>
+template <bool BWD, bool TAN>
 __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ TcbArgs a) {
     constexpr int NB = BWD ? 1 : 2;   // accumulator buffers
     constexpr int RX = ring_x(BWD), RP = ring_p(BWD);
@@ -462,7 +463,9 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
     const long long ntiles = (ncols + TN - 1) / TN;
     const long long g = gridDim.x;
     const unsigned limit = a.wait_limit ? a.wait_limit : kWaitLimit;
-    const bool tangent = !(a.mode & TCB_NO_TANGENT);
+    // the tangent components are carried (else zero and left out): fixed at
+    // compile time in the backward kernel, read from the mode forward
+    const bool tangent = BWD ? TAN : !(a.mode & TCB_NO_TANGENT);
     const int dir = BWD ? 1 : 0;
 
     if (mma_warp) {
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             unsigned char* xb = xslots + sg * kXSlot;
             float* cs = csc + (int)(j & 3) * NE;
             const unsigned kb = (ub >> 2) * kLboX + (ub & 3u) * 4u;
-            if constexpr (BWD) slice_cols_call(xb, cs, kb, uq, lane, tangent, xr[0], xr[1], xr[2], xr[3]);
+            if constexpr (BWD) slice_cols_call<TAN>(xb, cs, kb, uq, lane, xr[0], xr[1], xr[2], xr[3]);
             else slice_cols_body(xb, cs, kb, uq, lane, tangent, xr);
             if (lane == 0) mbar_arrive(&bars[B_SCALES0 + (int)(j & 3)]);
             fence_async_smem();
@@ -933,10 +936,11 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
 int tcb_tiles(long long ncols, bool /*bwd*/) { return (int)((ncols + TN - 1) / TN); }
 
 cudaError_t tcb_set_smem_limits() {
-    cudaError_t e = cudaFuncSetAttribute(tcb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)launch_smem(false));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tcb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)launch_smem(true));
+    const cudaFuncAttribute attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(tcb_kernel<false, true>, attr, (int)launch_smem(false));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tcb_kernel<true, true>, attr, (int)launch_smem(true));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tcb_kernel<true, false>, attr, (int)launch_smem(true));
+    return e;
 }
 
 namespace {
@@ -1003,8 +1007,10 @@ cudaError_t launch_tcb(const TcbArgs& args, bool bwd, int ctas, cudaStream_t st)
     a.tma_x = encode_state_map(&a.tm_x, a.xin, bl, a.ncols);
     a.tma_p = bwd && encode_state_map(&a.tm_p, a.psi, bl, a.ncols);
     const unsigned smem = launch_smem(bwd);
-    if (bwd) tcb_kernel<true><<<ctas, kT + 32, smem, st>>>(a);
-    else tcb_kernel<false><<<ctas, kT + 32, smem, st>>>(a);
+    const bool tan = !(a.mode & TCB_NO_TANGENT);
+    if (bwd && tan) tcb_kernel<true, true><<<ctas, kT + 32, smem, st>>>(a);
+    else if (bwd) tcb_kernel<true, false><<<ctas, kT + 32, smem, st>>>(a);
+    else tcb_kernel<false, true><<<ctas, kT + 32, smem, st>>>(a);   // (forward: the mode decides)
     return cudaGetLastError();
 }
 
