@@ -111,13 +111,14 @@ enum : int {
     B_FREE0 = 6,    // the epilogue has read accumulator buffer 0 (256 arrivals)
     B_FREE1 = 7,    // ... buffer 1
     B_CREADY = 8,   // backward: the tile's co-states are in the TF32 buffer (256 epilogue arrivals)
-    B_PREADY = 9,   // backward: the tile's forward states are in the TF32 buffer and the previous
-                    //   environment is read (256 producer arrivals)
-    B_DONE_E = 10,  // backward: the environment MMAs complete (commit)
+    B_PREADY = 9,   // backward, even tiles: the previous pair's environment is read (256 producer
+                    //   arrivals), so that the tile's environment may start afresh
+    B_DONE_E = 10,  // backward: the environment MMAs of an even tile complete (commit)
     B_DRAIN = 11,   // every MMA issued so far complete (commit, on the way out after a failed wait)
     B_RING0 = 12,   // ring slot s (B_RING0 + s, 4 slots): every producer's copies into it complete
     B_SCALES0 = 16, // column scales of tile j in scale slot j mod 4 (B_SCALES0 + slot; 8 producer warps)
-    B_COUNT = 20
+    B_DONE_E1 = 20, // backward: the environment MMAs of an odd tile complete (commit)
+    B_COUNT = 21
 };
 
 // Shared-memory layout (bytes, from a 1024-byte aligned base): the raw-tile
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
         const unsigned rx = xgen ? 256u : 1u, rp = pgen ? 256u : 1u;
         const unsigned r2 = RX > 2 ? rx : rp, r3 = RX > 3 ? rx : rp;
         const unsigned counts[B_COUNT] = {256u, 256u, cm, cm, cm, cm, 256u, 256u, 256u, 256u,
-                                          cm, 1u, rx, rx, r2, r3, 8u, 8u, 8u, 8u};
+                                          cm, 1u, rx, rx, r2, r3, 8u, 8u, 8u, 8u, cm};
         for (int i = 0; i < B_COUNT; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[i])), "r"(counts[i]));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             // high x high + high x low + low x high. The environments of two
             // consecutive tiles (local 2m and 2m + 1) accumulate in TMEM
             // before the producers read them.
-            auto env = [&](bool onto) {
+            auto env = [&](bool onto, int done) {
                 const unsigned ps = smem_u32(psislots), ds = smem_u32(dbuf);
                 const uint64_t ph = sdesc(ps, kLboE, kSboE), pl = sdesc(ps + kERegion, kLboE, kSboE);
                 const uint64_t dh = sdesc(ds, kLboE, kSboE), dl = sdesc(ds + kERegion, kLboE, kSboE);
@@ -611,15 +612,15 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                     mma_ss_tf32(tb + kEnvCol, dh + k * ke, pl + k * ke, id_e, 1);
                     mma_ss_tf32(tb + kEnvCol, dl + k * ke, ph + k * ke, id_e, 1);
                 }
-                mma_commit(&bars[B_DONE_E]);
+                mma_commit(&bars[done]);
             };
             // the environment of tile j once its co-states and forward states are staged
             auto env_of = [&](long long j) -> bool {
                 if (!wait(B_CREADY, (unsigned)(j & 1))) return false;
                 if (a.tma_p) issue_tma(j + RP, true);   // every epilogue thread has read Psi slot j mod RP
-                if (!wait(B_PREADY, (unsigned)(j & 1))) return false;
+                if ((j & 1) == 0 && !wait(B_PREADY, (unsigned)((j >> 1) & 1))) return false;
                 tc_fence_after();
-                env((j & 1) != 0);   // odd tiles add onto the even tile before them
+                env((j & 1) != 0, (j & 1) ? B_DONE_E1 : B_DONE_E);   // odd tiles add onto the even tile before them
                 return true;
             };
             if (a.tma_x)   // the ring's first tiles
@@ -776,16 +777,21 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
                 produce_x(j + 1, sg);
             }
             if (BWD) {
-                // every tile waits for the previous tile's environment MMAs
-                // (PREADY then never runs two phases ahead of the MMA warp's
-                // wait); the sums are read after odd tiles (tiles j - 2 and
-                // j - 1) and after the last
-                if (j >= 1) {
-                    if (!wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
+                // the sums are read after each pair of tiles (j - 2, j - 1)
+                // and after the last tile, once its environment MMAs are
+                // complete (even and odd tiles commit to barriers of their
+                // own, so that each is waited for phase by phase); then an
+                // even tile's environment may start afresh (PREADY, which
+                // never runs two phases ahead of the MMA warp's wait: the
+                // next arrival follows the read of an environment issued
+                // after that wait)
+                if (j >= 1 && (((j - 1) & 1) || last)) {
+                    const long long t = j - 1;
+                    if (!wait((t & 1) ? B_DONE_E1 : B_DONE_E, (unsigned)((t >> 1) & 1))) bad = true;
                     tc_fence_after();
-                    if (((j - 1) & 1) || last) read_env(last);
+                    read_env(last);
                 }
-                if (!last) {
+                if (!last && (j & 1) == 0) {
                     tc_fence_before();
                     mbar_arrive(&bars[B_PREADY]);
                 }
@@ -910,7 +916,7 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             if constexpr (BWD) {
                 // the co-states as the TF32 operand of the environment GEMM,
                 // once the previous environment MMAs have read the buffer
-                if (j >= 1 && !wait(B_DONE_E, (unsigned)((j - 1) & 1))) bad = true;
+                if (j >= 1 && !wait(((j - 1) & 1) ? B_DONE_E1 : B_DONE_E, (unsigned)(((j - 1) >> 1) & 1))) bad = true;
                 const unsigned ub = (unsigned)lane;
                 const unsigned base = (unsigned)e * kLboE + (ub >> 1) * kSboE + (ub & 1u) * 64u;
                 float4 o[4];
