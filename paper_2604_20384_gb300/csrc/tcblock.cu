@@ -905,12 +905,21 @@ __global__ void __launch_bounds__(kT + 32) tcb_kernel(const __grid_constant__ Tc
             // contiguous bytes per warp instruction for bl >= 5)
             const long long c0 = tile * TN;
             if (!(BWD && (a.mode & TCB_NO_STORE))) {
-                const unsigned bmk = (1u << bm) - 1u;
+                if (bm == 5) {   // lane = column, block indices 4 e + k: one base, 2^bl apart
+                    if (c0 + lane < ncols) {
+                        float4* p = a.xout + amp_index(c0 + lane, 4u * (unsigned)e, bl);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned f = (unsigned)(32 * (4 * e + k) + lane);
-                    const unsigned c = (f & bmk) | ((f >> (bm + 5)) << bm), b = (f >> bm) & 31u;
-                    if (c0 + c < ncols) __stcs(&a.xout[amp_index(c0 + c, b, bl)], out(b, c));
+                        for (int k = 0; k < 4; ++k)
+                            __stcs(p + ((size_t)k << bl), out(4u * (unsigned)e + (unsigned)k, (unsigned)lane));
+                    }
+                } else {
+                    const unsigned bmk = (1u << bm) - 1u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const unsigned f = (unsigned)(32 * (4 * e + k) + lane);
+                        const unsigned c = (f & bmk) | ((f >> (bm + 5)) << bm), b = (f >> bm) & 31u;
+                        if (c0 + c < ncols) __stcs(&a.xout[amp_index(c0 + c, b, bl)], out(b, c));
+                    }
                 }
             }
             if constexpr (BWD) {
