@@ -534,7 +534,7 @@ int enqueue_tensor(hvp_ctx* c, bool tan) {
                                      tan ? 1 : 0, frob ? 1 : 0, c->stream));
     if ((rc = prof_mark(c, HVP_K_POST, 0.0, 0.0))) return rc;
     L += 4;
-    c->launches_per_call[tan ? 1 : 0] = L + 1;   // + the status reset
+    c->launches_per_call[tan ? 1 : 0] = L;   // kernels (the status reset is a memset)
     return HVP_OK;
 }
 
@@ -546,10 +546,12 @@ int enqueue_all(hvp_ctx* c, bool tan) {
                                          c->cfg.n_layers, c->stream));
     if (c->tensor) {
         if ((rc = enqueue_tensor(c, tan))) return rc;
-        if (c->ti)
+        if (c->ti) {
             CUDA_TRY(c, launch_contract_layers(reinterpret_cast<const double2*>(c->d_res + c->off_ge()),
                                                reinterpret_cast<double2*>(c->d_res + c->off_layer()),
                                                c->d_layer_first, c->cfg.n_layers, c->K, c->stream));
+            c->launches_per_call[tan ? 1 : 0] += 2;   // the layer expansion and contraction
+        }
         return HVP_OK;
     }
     CUDA_TRY(c, launch_prep(c->d_G, tan ? c->d_V : nullptr, c->d_mats, c->dbl, c->K, c->d_status, c->stream));
