@@ -157,3 +157,8 @@ def test_tensor_headline_shape_against_oracle_on_all_samples():
     with native.Context(20, 16, w.psi1q, w.Uref, tensor=True) as ctx:
         assert ctx.plan_info()["passes"] == 26
         _check(ctx, w, o)
+        # the tangent-free kernels (a kernel of their own in the backward) at
+        # 431 and 432 tiles per CTA: loss and gradient alone
+        loss, grad = ctx.loss_grad(w.G)
+        assert abs(loss - o["loss"]) <= TOL
+        assert rel(grad, o["grad"]) < TOL
