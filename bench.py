@@ -426,8 +426,8 @@ def tensor_roofline(by_kind, info, total_ms, peaks, src):
                             "sustained bf16 cuBLAS rate"}}
 
     roofline = dict(_rate(bw), bound="hbm", traffic=recorded_traffic(info, "tensor"), peak_source=src,
-                    kernel="tcb_kernel<1, 1> (backward fused 5-qubit block with tangents: exact-integer bf16 slice GEMM and TF32 "
-                           "environment GEMM on tcgen05, TMA tile loads)")
+                    kernel="tcb_kernel<1, 1> (backward fused 5-qubit block with tangents: exact-integer bf16 "
+                           "slice GEMM and TF32 environment GEMM on tcgen05, TMA tile loads)")
     roofline["forward_kernel"] = _rate(fw)
     all_by = bw["bytes"] + fw["bytes"]
     all_ms = bw["ms"] + fw["ms"]
