@@ -67,8 +67,9 @@ extern "C" {
 #define HVP_NO_GRAPH 8    /* launch kernels directly instead of a CUDA graph
                              (each pass is then also an NVTX range, named
                              with its index; every call is one)            */
-#define HVP_AUTOTUNE 16   /* time the window/threads/arithmetic candidates at
-                             hvp_init and keep the fastest (see hvp_plan_info) */
+#define HVP_AUTOTUNE 16   /* time the window/threads/arithmetic candidates and
+                             the fused-block tensor-core schedule at hvp_init
+                             and keep the fastest (see hvp_plan_info)        */
 #define HVP_FROBENIUS 32  /* loss, gradient and HVP of the sampled Frobenius
                              cost C_F = 1 - (1/N_s) sum_s Re T_s (Eq. Frobenius,
                              Eq. grad-costF, Eq. hvp-costF) instead of C      */
@@ -82,10 +83,12 @@ extern "C" {
                              sharing one sweep; windows of at most 11 qubits */
 #define HVP_TENSOR 256    /* fused-block schedule on the tensor cores: the gates
                              are grouped into blocks of 5 neighbouring qubits
-                             (App. D's block-triangular [[B, 0], [dB, B]] per
-                             block), each block applied to all states as a
-                             real 128 x 128 GEMM with three TF32 products per
-                             FP32 product (tcgen05, sm_103a), the forward states
+                             (App. D's block operator B and its tangent dB),
+                             each block applied to all states as the real
+                             GEMM [B ; dB] [psi | dpsi] (128 x 64 x 64 per
+                             tile of 32 columns) on exact-integer bf16 slices
+                             of both operands (tcgen05, sm_103a), the block
+                             environments as a TF32 GEMM, the forward states
                              at every block boundary kept in device memory
                              ((blocks + 1) * 16 * 2^n * N_s bytes), the
                              co-states weighted by T_s and Omega_s so that the
