@@ -2,10 +2,10 @@
 FP64 oracle, element by element.
 
 The schedule groups the gates into blocks of five neighbouring qubits (App.
-D's block-triangular operator per block), applies each block as a real
-128 x 128 GEMM with three TF32 products per FP32 product on tcgen05, and
-weights the co-states by the overlaps so that block environments sum over
-samples. Bar: 1e-5 relative (Frobenius norm over all K blocks) for the
+D's block operator B and its tangent dB), applies each block as the real
+GEMM [B ; dB] [psi | dpsi] on exact-integer bf16 slices of both operands on
+tcgen05 (the block environments as a TF32 GEMM), and weights the co-states
+by the overlaps so that block environments sum over samples. Bar: 1e-5 relative (Frobenius norm over all K blocks) for the
 gradient and the HVP, the mean fidelity 1 - C relatively and C absolutely, as
 for the other complex64 paths.
 """
